@@ -1,0 +1,354 @@
+"""Online solves/s of the method of polarized traces on one GB300 (or N replicas).
+
+A step is one online solve (Algorithm 2: interface right-hand side by local
+solves, flexible GMRES to the relative residual 1e-7 with the Gauss-Seidel
+sweep preconditioner, volume reconstruction) of one batch of synthetic point
+sources with the offline data (local factors, interface Green's matrices)
+already resident in HBM.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
+
+Multi-GPU: sources are independent right-hand sides, so N ranks run N
+replicas (each builds its own offline data and solves its own batch); no
+collective is on the data path, the ranks only meet at the timing barriers.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "solves/s at rel. residual 1e-7 (online GMRES), chosen form vs plain FP64, 1 GB300"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 issue rate: 2 FMA per clock per SM (measured with a dependent-free FMA loop),
+# 152 SMs, 2070 MHz maximum SM clock, 2 flops per FMA.
+FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(gpus: int):
+    """Rank / world from torchrun; gloo for the timing barriers (no data collective)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def sources_for(wl: W.Workload, count: int) -> np.ndarray:
+    """The workload's sources, repeated (shifted one node right each time) to fill a batch."""
+    pos = list(wl.sources)
+    out = []
+    k = 0
+    while len(out) < count:
+        p, q = pos[k % len(pos)]
+        out.append((min(wl.nx, p + k // len(pos)), q))
+        k += 1
+    return W.point_sources(wl.nt, wl.Nz, wl.npml, wl.h, out)
+
+
+def cpu_baseline(wl: W.Workload, sample_solves: int, c: np.ndarray, omega: float):
+    """The oracle's plain definition of the solve (global sparse LU, Section 2.1) on the host cores:
+    factorization once (excluded, like the GPU offline phase), then back-substitutions timed."""
+    from oracle import discretization as D
+    from oracle import solver as S
+
+    prob = D.make_problem(c, wl.npml, wl.h, omega)
+    t0 = time.perf_counter()
+    lu = S.global_factor(prob)
+    t_fact = time.perf_counter() - t0
+    f = sources_for(wl, sample_solves)
+    t0 = time.perf_counter()
+    for s in range(sample_solves):
+        lu.solve(f[s].reshape(-1))
+    dt = time.perf_counter() - t0
+    return {"value": sample_solves / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_solves} back-substitutions with the global SuperLU factorization of the same "
+                      f"{wl.name} problem (factorization {t_fact:.1f} s excluded; SciPy SuperLU is single-threaded)"}
+
+
+def run_reference(args, wl, rank, world, pg):
+    """--impl reference: the CPU oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    c = wl.c_ext()
+    om = wl.omega(c)
+    from oracle import discretization as D
+    from oracle import solver as S
+
+    prob = D.make_problem(c, wl.npml, wl.h, om)
+    lu = S.global_factor(prob)
+    f = sources_for(wl, args.sources)
+    for _ in range(args.warmup):
+        for s in range(args.sources):
+            lu.solve(f[s].reshape(-1))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in range(args.sources):
+            lu.solve(f[s].reshape(-1))
+    dt = time.perf_counter() - t0
+    value = args.steps * args.sources / dt
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "sources_per_step": args.sources},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.sources} back-substitution(s) per step with the global SuperLU "
+                                       "factorization (factorization excluded)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=W.GRF_511x1023.name, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--sources", type=int, default=1, help="sources per step (batch)")
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--cpu-sample", type=int, default=20, help="oracle back-substitutions in cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = W.WORKLOADS[args.workload]
+    rank, world, local, pg = dist_setup(args.gpus)
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world, pg)
+        return
+
+    import torch
+
+    from paper_1410_5910_gb300 import PT_FP64, PT_MIXED_FP32, PolarTrace, default_pml_strength
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tol = args.tol if args.tol is not None else wl.tol
+    c = wl.c_ext()
+    om = wl.omega(c)
+    pmlC = default_pml_strength(float(c.max()))
+    c_dev = torch.from_numpy(c).to(dev)
+    S = args.sources
+    f_host = sources_for(wl, S)
+    f_dev = torch.from_numpy(f_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(prec):
+        t0 = time.perf_counter()
+        s = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, om, c_dev, pml_C=pmlC, precision=prec, max_sources=S,
+                       max_krylov=40)
+        torch.cuda.synchronize(dev)
+        return s, time.perf_counter() - t0
+
+    def time_solves(solver, steps, warmup):
+        u = torch.empty_like(f_dev)
+        its = None
+        for _ in range(warmup):
+            _, _, its, rel = solver.solve(f_dev, tol=tol, u=u, want_traces=False)
+        barrier(pg)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                _, _, its, rel = solver.solve(f_dev, tol=tol, u=u, want_traces=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        barrier(pg)
+        ms = e0.elapsed_time(e1)
+        return ms / steps, its, rel, u, clk.summary()
+
+    chosen_prec = PT_MIXED_FP32 if args.precision == "mixed" else PT_FP64
+    solver, t_off = make(chosen_prec)
+    ms_local, its, rel, u, clocks = time_solves(solver, args.steps, args.warmup)
+    launches, _ = solver.last_solve_stats()
+    ms = max_over_ranks(pg, ms_local)
+    total_solves = sum_over_ranks(pg, float(S))  # per step, all ranks
+    value = total_solves / (ms / 1e3)
+
+    # plain FP64 form on the same workload, and the volume difference of the chosen form against it
+    extra = {}
+    plain = None
+    fp64_solver = solver
+    if not args.no_plain and chosen_prec != PT_FP64:
+        fp64_solver, t_off64 = make(PT_FP64)
+        ms64, its64, rel64, u64, _ = time_solves(fp64_solver, max(2, args.steps // 2), 3)
+        diff = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+        plain = {"value": total_solves / (max_over_ranks(pg, ms64) / 1e3),
+                 "ms_per_step": ms64, "gmres_iterations": its64, "true_relres": rel64, "offline_s": t_off64}
+        extra["volume_rel_diff_vs_fp64"] = diff
+
+    # ---- roofline of the block-apply kernel (the interface-system matvec, one launch) ----
+    pk, pk_kind = peaks()
+    x = torch.randn((S, fp64_solver.T4, fp64_solver.nt), dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        fp64_solver.matvec(x)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a_, b_ in ev:
+        a_.record(stream)
+        fp64_solver.matvec(x)
+        b_.record(stream)
+    torch.cuda.synchronize(dev)
+    t_launch = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
+    L_ = wl.L
+    nblocks = 16 * (L_ - 2) + 8
+    nt = wl.nt
+    flops = 8.0 * nblocks * nt * nt * S
+    roof = {"kernel": "apply_kernel<double2> (interface-system matvec P M x, FP64 blocks)", "bound": "alu",
+            "achieved": flops / t_launch / 1e12, "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
+            "frac": None, "traffic": None, "peak_source": "FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz",
+            "algorithmic_bytes": nblocks * nt * nt * 16 + 2 * 4 * (L_ - 1) * nt * 16 * S,
+            "achieved_hbm_gbs": (nblocks * nt * nt * 16) / t_launch / 1e9, "launch_ms": t_launch * 1e3}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    # ---- end to end through the host-buffer entry point (pinned memory) ----
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    scratch = torch.empty(solver.host_scratch_bytes(), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        solver.solve_host(f_pin, u_pin, tol=tol, scratch=scratch)
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve_host(f_pin, u_pin, tol=tol, scratch=scratch)
+    dt = max_over_ranks(pg, time.perf_counter() - t0)
+    e2e = {"value": total_solves * args.steps / dt, "unit": "solves/s",
+           "h2d_bytes_per_step": int(f_pin.numel() * 16), "d2h_bytes_per_step": int(u_pin.numel() * 16)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_sample, c, om)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if chosen_prec == PT_FP64 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "nx": wl.nx, "nz": wl.nz, "npml": wl.npml, "L": wl.L,
+                       "medium": wl.medium, "omega": om, "sources_per_step": S, "tol": tol,
+                       "form": "mixed FP32 preconditioner, FP64 FGMRES" if chosen_prec else "plain FP64",
+                       "blocks": "dense", "parallelism": f"replicas x{world}",
+                       "l2": f"interface blocks {16 * L_ * nt * nt * 16 / 1e9:.2f} GB stream from HBM each "
+                             "iteration (> 129 MB L2); no flush needed"},
+            "gmres_iterations": its, "true_relres": rel, "offline_s": t_off,
+            "roofline": roof, "peaks_source": pk_kind, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": int(launches * args.steps), "cpu_baseline": cpu,
+        }
+        if plain is not None:
+            line["plain_fp64"] = plain
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

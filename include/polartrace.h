@@ -1,0 +1,178 @@
+/*
+ * polartrace.h - C ABI of the GB300 (sm_103a) implementation of the method of
+ * polarized traces for the 2D Helmholtz equation (Zepeda-Nunez & Demanet,
+ * "The method of polarized traces for the 2D Helmholtz equation", 2014).
+ *
+ * Problem statement (Section 2.1): find u on the extended grid
+ * (n_x + 2 n_pml) x (n_z + 2 n_pml) with
+ *     -alpha_x d_x(alpha_x d_x u) - alpha_z d_z(alpha_z d_z u) - omega^2 u / c^2 = f,
+ * 5-point finite differences of step h, PML profile sigma = (C/delta)(d/delta)^2
+ * (delta = n_pml h) and homogeneous Dirichlet data one node outside the grid.
+ * The z axis is split into L layers (Section 2.2); the online solve
+ * (Algorithm 2) forms the interface right-hand side by local solves, solves
+ * the polarized jump system (Definition 9) by GMRES preconditioned with
+ * Algorithm 4, and rebuilds the volume field by local solves.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns pt_status; none aborts, throws or exits.
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *    buffer; the library keeps device pointers only between pt_create and
+ *    pt_destroy and never allocates device memory (scratch comes from the
+ *    caller through the workspace arguments).
+ *  - Complex numbers are pt_c128 {re, im} (16 bytes, interleaved).
+ *  - Volume arrays are row-major [z][x] on the extended grid (x fastest):
+ *    element (p, q) of the paper (p, q = -n_pml+1 .. n+n_pml) sits at index
+ *    (q + n_pml - 1) * n_t + (p + n_pml - 1), n_t = n_x + 2 n_pml,
+ *    N_z = n_z + 2 n_pml.  Several sources are stacked as [source][z][x].
+ *  - Interface traces are laid out [source][dir][interface][trace][x]:
+ *    dir 0 = down-going, 1 = up-going (Section 3.2); interface i = 0..L-2
+ *    lies between layers i and i+1 (0-based); trace 0 is the last row of
+ *    layer i (u^i_n = u^{i+1}_0), trace 1 the first row of layer i+1
+ *    (u^i_{n+1} = u^{i+1}_1); x runs over n_t columns.
+ *  - All device work is ordered on the stream given to pt_create.
+ *    pt_solve and pt_solve_host synchronise that stream once per GMRES
+ *    iteration to read the residual estimate and return only when done.
+ */
+#ifndef POLARTRACE_H
+#define POLARTRACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_ctx pt_ctx;
+
+typedef struct {
+  double re, im;
+} pt_c128;
+
+typedef enum {
+  PT_OK = 0,
+  PT_ERR_ARG = 1,           /* invalid argument; nothing was launched          */
+  PT_ERR_WORKSPACE = 2,     /* a workspace / scratch buffer is too small        */
+  PT_ERR_CUDA = 3,          /* a CUDA runtime call failed                       */
+  PT_ERR_SINGULAR = 4,      /* zero pivot in a local factorization              */
+  PT_ERR_NOT_CONVERGED = 5, /* GMRES hit max_it; outputs hold the best iterate  */
+  PT_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up               */
+  PT_ERR_NUMERIC = 7        /* NaN/Inf met in the data                          */
+} pt_status;
+
+typedef enum {
+  PT_FP64 = 0,      /* every block product in FP64                                   */
+  PT_MIXED_FP32 = 1 /* preconditioner (Algorithm 4) applies FP32 copies of the blocks;
+                       the GMRES matvec, Arnoldi, least squares and the true
+                       residual stay FP64 (flexible GMRES)                           */
+} pt_precision;
+
+typedef struct {
+  int32_t nx, nz;   /* interior grid points (Section 2.1)                          */
+  int32_t npml;     /* PML points on each side, n_pml = delta / h                   */
+  int32_t L;        /* number of layers (Section 2.2)                               */
+  double h;         /* grid step                                                    */
+  double omega;     /* angular frequency                                            */
+  double pml_C;     /* PML strength C of sigma = (C/delta)(d/delta)^2               */
+  int32_t precision;  /* pt_precision                                               */
+  int32_t gs_iters;   /* n_it of Algorithm 4 (the paper uses 2)                      */
+  int32_t max_sources;/* largest nsrc a pt_solve call may use                       */
+  int32_t max_krylov; /* largest GMRES iteration count a pt_solve call may use      */
+} pt_params;
+
+/* Layer partition used by the library (Section 2.2): the first (N_z mod L)
+ * layers get one extra row.  row_start must hold L+1 ints (host); on return
+ * row_start[l] is the first extended-grid row of layer l and row_start[L] = N_z.
+ * Fails with PT_ERR_ARG when an interface would lie within one row of the
+ * PML or a layer would have fewer than 3 rows. */
+pt_status pt_layer_partition(const pt_params* prm, int32_t* row_start);
+
+/* Device memory the caller must provide (bytes, host outputs):
+ *   persistent_bytes : kept from pt_create to pt_destroy (local factors,
+ *                      interface Green's matrices, tables);
+ *   setup_bytes      : temporary, used only inside pt_create;
+ *   solve_bytes      : scratch for one pt_solve call with max_sources sources
+ *                      and max_krylov iterations.
+ * Any output pointer may be NULL. */
+pt_status pt_workspace_size(const pt_params* prm, size_t* persistent_bytes, size_t* setup_bytes,
+                            size_t* solve_bytes);
+
+/* Offline phase (Algorithm 1) on the GPU, in FP64: assembles every local
+ * problem H^l (Section 2.2, padded PML, normal extension of m = 1/c^2),
+ * factors it along x by block elimination with pivoted Gauss-Jordan
+ * inversion of the Schur complements, and extracts the interface Green's
+ * matrices G^l(z_j, z_k), j, k in {0, 1, n, n+1} (Definition 1) by solves
+ * with identity columns.
+ *   c_ext      device, N_z * n_t doubles, wave speed c > 0 on the extended grid
+ *   persistent device, >= persistent_bytes, 256-byte aligned
+ *   setup      device, >= setup_bytes, 256-byte aligned (free after return)
+ *   stream     cudaStream_t (may be NULL for the legacy default stream)
+ *   out        host, receives the context
+ * Errors: PT_ERR_ARG (sizes, partition, h/omega/C not positive, alignment),
+ * PT_ERR_WORKSPACE, PT_ERR_NUMERIC (c not finite or not positive),
+ * PT_ERR_SINGULAR (zero pivot), PT_ERR_CUDA.  Blocks until done. */
+pt_status pt_create(const pt_params* prm, const double* c_ext, void* persistent, size_t persistent_bytes,
+                    void* setup, size_t setup_bytes, void* stream, pt_ctx** out);
+
+/* Online phase (Algorithm 2) for nsrc right-hand sides, all device pointers:
+ *   f        device, nsrc * N_z * n_t pt_c128 sources
+ *   u        device, nsrc * N_z * n_t pt_c128 volume field out (NULL: skip
+ *            the reconstruction step)
+ *   traces   device, nsrc * 4 (L-1) n_t pt_c128 polarized traces out (NULL: skip)
+ *   rel_tol  GMRES stops when the flexible GMRES least-squares estimate is
+ *            <= rel_tol * ||P b|| and the explicit FP64 residual confirms it
+ *   max_it   <= max_krylov
+ *   scratch  device, >= solve_bytes
+ *   iters    host, nsrc ints: GMRES iterations per source (may be NULL)
+ *   relres   host, nsrc doubles: true relative residual of the polarized
+ *            system per source (may be NULL)
+ * Returns PT_ERR_NOT_CONVERGED (with outputs written) when some source did
+ * not reach rel_tol within max_it iterations. */
+pt_status pt_solve(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* u, pt_c128* traces, double rel_tol,
+                   int32_t max_it, void* scratch, size_t scratch_bytes, int32_t* iters, double* relres);
+
+/* Same as pt_solve with f and u in HOST memory (pinned memory gives the best
+ * copy rate); the library copies them through the scratch buffer, whose size
+ * must be >= solve_bytes + 2 * nsrc * N_z * n_t * 16 bytes. */
+pt_status pt_solve_host(pt_ctx* ctx, int32_t nsrc, const pt_c128* f_host, pt_c128* u_host, double rel_tol,
+                        int32_t max_it, void* scratch, size_t scratch_bytes, int32_t* iters, double* relres);
+
+/* Building blocks of the online phase, exposed for testing and composition.
+ * All pointers device; x, y hold nsrc polarized-trace vectors in the layout
+ * above.  Each applies the FP64 blocks.
+ *   pt_apply_matvec       y = P M x  (Definition 9, permuted: D + R)
+ *   pt_apply_precond      y = Algorithm 4 applied to the permuted residual x
+ *                         (n_it = gs_iters; uses the context's precision)
+ *   pt_apply_D_inverse    y = D^{-1} x (the two sweeps of Section 4.1)
+ *   pt_apply_R            y = R x
+ *   pt_rhs                y = P b, b = (-f, -f_0) from the local Newton
+ *                         potentials of f (device, nsrc * N_z * n_t)
+ * scratch >= solve_bytes. */
+pt_status pt_apply_matvec(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y);
+pt_status pt_apply_precond(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y, void* scratch,
+                           size_t scratch_bytes);
+pt_status pt_apply_D_inverse(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y);
+pt_status pt_apply_R(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y);
+pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y, void* scratch, size_t scratch_bytes);
+
+/* Copy the interface Green's matrix G^l(z_j, z_k) / h (the block that the
+ * incomplete Green's integrals of Definition 2 multiply) to dst (device,
+ * n_t * n_t pt_c128, row-major, row = target node, column = source node).
+ * j, k are the paper's local row indices and must be among {0, 1, n^l, n^l+1}
+ * of the layer's interfaces.  Fails with PT_ERR_ARG otherwise. */
+pt_status pt_get_block(pt_ctx* ctx, int32_t layer, int32_t j, int32_t k, pt_c128* dst);
+
+/* Statistics of the last pt_solve: number of kernel launches it issued and
+ * the GMRES iteration count of the slowest source. */
+pt_status pt_last_solve_stats(const pt_ctx* ctx, int64_t* kernel_launches, int32_t* max_iterations);
+
+void pt_destroy(pt_ctx* ctx);
+const char* pt_status_string(pt_status s);
+/* Text of the last error recorded on this thread (empty when none). */
+const char* pt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLARTRACE_H */

@@ -126,3 +126,9 @@ def online_solve(off: Offline, f: np.ndarray, tol: float = 1e-7, max_it: int = 6
         rel = np.linalg.norm(b - A(x)) / np.linalg.norm(b)
     u = reconstruct(off, f, polarized.collapse(x, off.L, off.prob.nt))
     return SolveResult(u, x, its, rel, hist)
+
+
+def global_factor(prob: Problem):
+    """Sparse LU of the global H (the factorization inside ``global_solve``), for timing
+    the per-source back-substitution separately from the factorization."""
+    return spla.splu(global_operator(prob).tocsc())

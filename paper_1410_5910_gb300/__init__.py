@@ -1,0 +1,177 @@
+"""GB300 (sm_103a) implementation of the method of polarized traces for the 2D Helmholtz equation.
+
+Python face of the C library ``libpolartrace`` (``include/polartrace.h``).
+PyTorch only provides device memory and the stream; every step of the method
+(offline factorisation and Green's-matrix extraction, the interface
+right-hand side, flexible GMRES with the Gauss-Seidel sweep preconditioner,
+the volume reconstruction) runs in the library's CUDA kernels.
+
+    solver = PolarTrace(nx, nz, npml, L, h, omega, c_ext_cuda)
+    u, traces, iters, relres = solver.solve(f_cuda, tol=1e-7)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from ._lib import PT_FP64, PT_MIXED_FP32, Params, PolarTraceError, check, lib
+
+__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "default_pml_strength", "layer_partition"]
+
+
+def default_pml_strength(c_max: float) -> float:
+    """C such that the continuous round trip through the PML damps speed c_max by 1e-6 (C = 1.5 c_max ln 1e6)."""
+    return 1.5 * c_max * math.log(1.0e6)
+
+
+def _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov) -> Params:
+    return Params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov)
+
+
+def layer_partition(nx, nz, npml, L) -> list:
+    """Row offsets of the library's layer split (Section 2.2)."""
+    p = _params(nx, nz, npml, L, 1.0, 1.0, 1.0, PT_FP64, 2, 1, 1)
+    out = (C.c_int32 * (L + 1))()
+    check(lib().pt_layer_partition(C.byref(p), out), "pt_layer_partition")
+    return list(out)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+class PolarTrace:
+    """An offline-prepared solver (Algorithm 1 on the GPU) for one medium and frequency."""
+
+    def __init__(self, nx: int, nz: int, npml: int, L: int, h: float, omega: float, c_ext: torch.Tensor,
+                 pml_C: float | None = None, precision: int = PT_FP64, gs_iters: int = 2, max_sources: int = 1,
+                 max_krylov: int = 40, stream: torch.cuda.Stream | None = None):
+        if not (c_ext.is_cuda and c_ext.dtype == torch.float64 and c_ext.is_contiguous()):
+            raise ValueError("c_ext must be a contiguous float64 CUDA tensor of shape (N_z, n_t)")
+        self.nx, self.nz, self.npml, self.L = nx, nz, npml, L
+        self.nt, self.Nz = nx + 2 * npml, nz + 2 * npml
+        if tuple(c_ext.shape) != (self.Nz, self.nt):
+            raise ValueError(f"c_ext must have shape {(self.Nz, self.nt)}")
+        if pml_C is None:
+            pml_C = default_pml_strength(float(c_ext.max()))
+        self.params = _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov)
+        self.max_sources, self.max_krylov = max_sources, max_krylov
+        self.device = c_ext.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        L_ = lib()
+        pb, sb, vb = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        check(L_.pt_workspace_size(C.byref(self.params), C.byref(pb), C.byref(sb), C.byref(vb)), "pt_workspace_size")
+        self.persistent_bytes, self.setup_bytes, self.solve_bytes = pb.value, sb.value, vb.value
+        self._persistent = torch.empty(pb.value, dtype=torch.uint8, device=self.device)
+        setup = torch.empty(max(sb.value, 256), dtype=torch.uint8, device=self.device)
+        self._scratch = torch.empty(max(vb.value, 256), dtype=torch.uint8, device=self.device)
+        ctx = C.c_void_p()
+        with torch.cuda.stream(self.stream):
+            check(L_.pt_create(C.byref(self.params), _ptr(c_ext), _ptr(self._persistent), pb.value, _ptr(setup),
+                               sb.value, C.c_void_p(self.stream.cuda_stream), C.byref(ctx)), "pt_create")
+        del setup
+        self._ctx = ctx
+        self.T4 = 4 * (L - 1)
+
+    def __del__(self):
+        ctx = getattr(self, "_ctx", None)
+        if ctx:
+            lib().pt_destroy(ctx)
+            self._ctx = None
+
+    # ---- online -----------------------------------------------------------
+    def _check_src(self, f: torch.Tensor) -> int:
+        if f.dim() == 2:
+            f = f.unsqueeze(0)
+        if not (f.is_cuda and f.dtype == torch.complex128 and f.is_contiguous()):
+            raise ValueError("f must be a contiguous complex128 CUDA tensor (S, N_z, n_t)")
+        if tuple(f.shape[1:]) != (self.Nz, self.nt):
+            raise ValueError(f"f must have shape (S, {self.Nz}, {self.nt})")
+        return f.shape[0]
+
+    def solve(self, f: torch.Tensor, tol: float = 1e-7, max_it: int | None = None, want_u: bool = True,
+              want_traces: bool = True, u: torch.Tensor | None = None, allow_not_converged: bool = False):
+        """Algorithm 2 for S sources.  Returns (u, traces, iterations, true relative residuals)."""
+        squeeze = f.dim() == 2
+        if squeeze:
+            f = f.unsqueeze(0)
+        S = self._check_src(f)
+        if max_it is None:
+            max_it = self.max_krylov
+        if want_u and u is None:
+            u = torch.empty_like(f)
+        tr = torch.empty((S, self.T4, self.nt), dtype=torch.complex128, device=self.device) if want_traces else None
+        iters = (C.c_int32 * S)()
+        rel = (C.c_double * S)()
+        st = lib().pt_solve(self._ctx, S, _ptr(f), _ptr(u) if want_u else None, _ptr(tr) if want_traces else None,
+                            tol, max_it, _ptr(self._scratch), self._scratch.numel(), iters, rel)
+        check(st, "pt_solve", allow=(5,) if allow_not_converged else ())
+        out_u = u if want_u else None
+        if squeeze:
+            out_u = out_u[0] if out_u is not None else None
+            tr = tr[0] if tr is not None else None
+        return out_u, tr, list(iters), list(rel)
+
+    def host_scratch_bytes(self) -> int:
+        return self.solve_bytes + 2 * self.max_sources * self.Nz * self.nt * 16 + 4096
+
+    def solve_host(self, f_host: torch.Tensor, u_host: torch.Tensor, tol: float = 1e-7, max_it: int | None = None,
+                   scratch: torch.Tensor | None = None):
+        """Algorithm 2 through pt_solve_host: f and u in host memory (pinned for full copy speed)."""
+        if f_host.is_cuda or u_host.is_cuda:
+            raise ValueError("solve_host takes host tensors")
+        S = f_host.shape[0]
+        if scratch is None:
+            scratch = torch.empty(self.host_scratch_bytes(), dtype=torch.uint8, device=self.device)
+        iters = (C.c_int32 * S)()
+        rel = (C.c_double * S)()
+        check(lib().pt_solve_host(self._ctx, S, _ptr(f_host), _ptr(u_host), tol, max_it or self.max_krylov,
+                                  _ptr(scratch), scratch.numel(), iters, rel), "pt_solve_host")
+        return list(iters), list(rel)
+
+    def last_solve_stats(self):
+        n = C.c_int64()
+        m = C.c_int32()
+        check(lib().pt_last_solve_stats(self._ctx, C.byref(n), C.byref(m)), "pt_last_solve_stats")
+        return n.value, m.value
+
+    # ---- building blocks (testing) -----------------------------------------
+    def _vec(self, S):
+        return torch.empty((S, self.T4, self.nt), dtype=torch.complex128, device=self.device)
+
+    def matvec(self, x: torch.Tensor) -> torch.Tensor:
+        y = torch.empty_like(x)
+        check(lib().pt_apply_matvec(self._ctx, x.shape[0], _ptr(x), _ptr(y)), "pt_apply_matvec")
+        return y
+
+    def apply_R(self, x: torch.Tensor) -> torch.Tensor:
+        y = torch.empty_like(x)
+        check(lib().pt_apply_R(self._ctx, x.shape[0], _ptr(x), _ptr(y)), "pt_apply_R")
+        return y
+
+    def apply_D_inverse(self, x: torch.Tensor) -> torch.Tensor:
+        y = torch.empty_like(x)
+        check(lib().pt_apply_D_inverse(self._ctx, x.shape[0], _ptr(x), _ptr(y)), "pt_apply_D_inverse")
+        return y
+
+    def precond(self, x: torch.Tensor) -> torch.Tensor:
+        y = torch.empty_like(x)
+        check(lib().pt_apply_precond(self._ctx, x.shape[0], _ptr(x), _ptr(y), _ptr(self._scratch),
+                                     self._scratch.numel()), "pt_apply_precond")
+        return y
+
+    def rhs(self, f: torch.Tensor) -> torch.Tensor:
+        if f.dim() == 2:
+            f = f.unsqueeze(0)
+        S = self._check_src(f)
+        y = self._vec(S)
+        check(lib().pt_rhs(self._ctx, S, _ptr(f), _ptr(y), _ptr(self._scratch), self._scratch.numel()), "pt_rhs")
+        return y
+
+    def block(self, layer: int, j: int, k: int) -> torch.Tensor:
+        """G^l(z_j, z_k) / h as an (n_t, n_t) complex128 CUDA tensor."""
+        out = torch.empty((self.nt, self.nt), dtype=torch.complex128, device=self.device)
+        check(lib().pt_get_block(self._ctx, layer, j, k, _ptr(out)), "pt_get_block")
+        return out

@@ -1,0 +1,731 @@
+// Host side of the C ABI declared in include/polartrace.h.
+//
+// pt_create runs Algorithm 1 (offline) and builds the operator tables of the
+// permuted polarized jump system P M = D + R (Section 3.5); pt_solve runs
+// Algorithm 2 with flexible GMRES (right preconditioned by Algorithm 4,
+// Section 4.2) driven from the host, one stream synchronisation per iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/polartrace.h"
+#include "pt_common.cuh"
+
+namespace pt {
+cudaError_t launch_check_medium(const double*, size_t, int*, cudaStream_t);
+cudaError_t launch_coef(const Geometry&, const LayerInfo*, const double*, cd*, cd*, cudaStream_t);
+cudaError_t launch_factor(const Geometry&, const LayerInfo*, int, const double*, cd*, int*, cudaStream_t);
+cudaError_t launch_extract(const Geometry&, const LayerInfo*, const ExtractTask*, int, int, int, const cd*,
+                           const cd*, const cd*, cd*, size_t, cd*, cudaStream_t);
+cudaError_t launch_to_fp32(const cd*, cf*, size_t, cudaStream_t);
+cudaError_t launch_apply(int, int, const ApplyRow*, int, bool, const void*, const cd*, const cd*, cd*, int, int,
+                         cudaStream_t);
+cudaError_t launch_layer_nonzero(const Geometry&, const LayerInfo*, const cd*, int*, int, cudaStream_t);
+cudaError_t launch_layer_solve(int, const Geometry&, const LayerInfo*, const cd*, const cd*, const cd*, const cd*,
+                               const cd*, cd*, size_t, cd*, const int*, int, cudaStream_t);
+int dot_chunks(size_t N);
+cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
+cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
+cudaError_t launch_norm_scale(const cd*, size_t, int, double*, cd*, int, int, int, int, cd*, size_t,
+                              cudaStream_t);
+cudaError_t launch_givens(int, int, int, cd*, double*, cd*, cd*, double*, cudaStream_t);
+cudaError_t launch_lsq_combine(int, int, const int*, const cd*, const cd*, cd*, const cd*, size_t, cd*,
+                               cudaStream_t);
+cudaError_t launch_sub(const cd*, const cd*, cd*, size_t, cudaStream_t);
+}  // namespace pt
+
+using namespace pt;
+
+static thread_local std::string g_last_error;
+
+static pt_status fail(pt_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define PT_CUDA(call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(PT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kExtractSlots = 152;
+constexpr int kApplyRowsSweep = 8;   // rows per CTA for the sweep steps
+constexpr int kApplyRowsWide = 16;   // rows per CTA for R and the matvec
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Plan {
+  Geometry g{};
+  int L = 0, nt = 0, Nz = 0, T = 0, T4 = 0;
+  size_t N = 0;  // entries of one polarized-trace vector
+  int nloc_max = 0;
+  std::vector<LayerInfo> layers;
+  std::vector<ExtractTask> tasks;
+  size_t sinv_elems = 0, coef_elems = 0;
+};
+
+pt_status make_plan(const pt_params* p, Plan& P) {
+  if (!p) return fail(PT_ERR_ARG, "params is NULL");
+  if (p->nx < 1 || p->nz < 1 || p->npml < 1 || p->L < 2 || p->L > kMaxLayers)
+    return fail(PT_ERR_ARG, "need nx, nz, npml >= 1 and 2 <= L <= 256");
+  if (!(p->h > 0) || !(p->omega > 0) || !(p->pml_C >= 0) || !std::isfinite(p->h) || !std::isfinite(p->omega) ||
+      !std::isfinite(p->pml_C))
+    return fail(PT_ERR_ARG, "h and omega must be positive, pml_C non-negative, all finite");
+  if (p->precision != PT_FP64 && p->precision != PT_MIXED_FP32) return fail(PT_ERR_ARG, "unknown precision");
+  if (p->gs_iters < 1 || p->gs_iters > 16) return fail(PT_ERR_ARG, "gs_iters must be in 1..16");
+  if (p->max_sources < 1 || p->max_krylov < 1 || p->max_krylov > 512)
+    return fail(PT_ERR_ARG, "max_sources >= 1 and 1 <= max_krylov <= 512");
+  P.nt = p->nx + 2 * p->npml;
+  P.Nz = p->nz + 2 * p->npml;
+  P.L = p->L;
+  P.T = 2 * (P.L - 1);
+  P.T4 = 4 * (P.L - 1);
+  P.N = (size_t)P.T4 * P.nt;
+  P.g = Geometry{P.nt, P.Nz, p->npml, P.L, p->h, p->omega, p->pml_C};
+  // near-equal split: the first (N_z mod L) layers get one extra row
+  const int base = P.Nz / P.L, extra = P.Nz % P.L;
+  int start = 0;
+  P.layers.resize(P.L);
+  for (int l = 0; l < P.L; ++l) {
+    LayerInfo& I = P.layers[l];
+    I.start = start;
+    I.n = base + (l < extra ? 1 : 0);
+    start += I.n;
+    I.has_top = l > 0;
+    I.has_bot = l < P.L - 1;
+    I.pad_top = I.has_top ? p->npml : 0;
+    I.pad_bot = I.has_bot ? p->npml : 0;
+    I.nloc = I.pad_top + I.n + I.pad_bot;
+    I.row[0] = I.has_top ? I.pad_top - 1 : -1;
+    I.row[1] = I.has_top ? I.pad_top : -1;
+    I.row[2] = I.has_bot ? I.pad_top + I.n - 1 : -1;
+    I.row[3] = I.has_bot ? I.pad_top + I.n : -1;
+    if (I.n < 3) return fail(PT_ERR_ARG, "every layer needs at least 3 rows");
+    if (l > 0 && !(I.start >= p->npml + 1 && I.start <= P.Nz - p->npml - 1))
+      return fail(PT_ERR_ARG, "an interface lies in or next to the PML; use fewer layers");
+    P.nloc_max = std::max(P.nloc_max, I.nloc);
+    I.sinv_off = (long long)P.sinv_elems;
+    I.coef_off = (long long)P.coef_elems;
+    P.sinv_elems += (size_t)P.nt * I.nloc * I.nloc;
+    P.coef_elems += (size_t)P.nt * I.nloc;
+  }
+  if (P.nloc_max > kMaxNloc)
+    return fail(PT_ERR_ARG, "a local problem has more than 118 rows (layer rows + 2 n_pml); use more layers");
+  // extraction tasks: 32 right-hand sides each
+  for (int l = 0; l < P.L; ++l) {
+    ExtractTask t{};
+    t.layer = l;
+    t.nk = 0;
+    if (P.layers[l].has_top) { t.kk[t.nk++] = 0; t.kk[t.nk++] = 1; }
+    if (P.layers[l].has_bot) { t.kk[t.nk++] = 2; t.kk[t.nk++] = 3; }
+    t.w = 32 / t.nk;
+    for (int c0 = 0; c0 < P.nt; c0 += t.w) {
+      t.c0 = c0;
+      P.tasks.push_back(t);
+    }
+  }
+  return PT_OK;
+}
+
+struct Persist {
+  LayerInfo* layers;
+  int* status;
+  cd* W;
+  cd* E;
+  cd* Sinv;
+  cd* blocks;
+  cf* blocks32;
+  ApplyRow* tab_matvec;
+  ApplyRow* tab_R;
+  ApplyRow* tab_sweep;
+  ExtractTask* tasks;
+};
+
+Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* bytes) {
+  Carver c(base);
+  Persist q{};
+  q.layers = c.take<LayerInfo>(P.L);
+  q.status = c.take<int>(64);
+  q.W = c.take<cd>(P.coef_elems);
+  q.E = c.take<cd>(P.coef_elems);
+  q.Sinv = c.take<cd>(P.sinv_elems);
+  const size_t bel = (size_t)P.L * 16 * P.nt * P.nt;
+  q.blocks = c.take<cd>(bel);
+  q.blocks32 = p->precision == PT_MIXED_FP32 ? c.take<cf>(bel) : nullptr;
+  q.tab_matvec = c.take<ApplyRow>(P.T4);
+  q.tab_R = c.take<ApplyRow>(P.T4);
+  q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
+  q.tasks = c.take<ExtractTask>(P.tasks.size());
+  if (bytes) *bytes = c.off;
+  return q;
+}
+
+size_t setup_slot_elems(const Plan& P) { return (size_t)P.nt * P.nloc_max * 32; }
+
+size_t setup_bytes_of(const Plan& P) {
+  Carver c(nullptr);
+  int nslots = std::min<int>((int)P.tasks.size(), kExtractSlots);
+  c.take<cd>(setup_slot_elems(P) * nslots);
+  return c.off;
+}
+
+struct SolveBufs {
+  cd* Y;
+  int* nzflag;
+  cd *b, *x, *w, *t, *u1, *V, *Z, *partial, *coef, *H, *sn, *g, *y;
+  double *cs, *resid, *nrm;
+  int* kk;
+  cd *fdev, *udev;  // pt_solve_host staging
+};
+
+SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base, size_t* bytes) {
+  Carver c(base);
+  SolveBufs b{};
+  const size_t N = P.N;
+  b.Y = c.take<cd>((size_t)S * P.L * P.nt * P.nloc_max);
+  b.nzflag = c.take<int>((size_t)S * P.L);
+  b.b = c.take<cd>(S * N);
+  b.x = c.take<cd>(S * N);
+  b.w = c.take<cd>(S * N);
+  b.t = c.take<cd>(S * N);
+  b.u1 = c.take<cd>(S * N);
+  b.V = c.take<cd>((size_t)(m + 1) * S * N);
+  b.Z = c.take<cd>((size_t)m * S * N);
+  b.partial = c.take<cd>((size_t)S * (m + 1) * dot_chunks(N));
+  b.coef = c.take<cd>((size_t)S * (m + 1));
+  b.H = c.take<cd>((size_t)S * (m + 1) * m);
+  b.sn = c.take<cd>((size_t)S * m);
+  b.g = c.take<cd>((size_t)S * (m + 1));
+  b.y = c.take<cd>((size_t)S * (m + 1));
+  b.cs = c.take<double>((size_t)S * m);
+  b.resid = c.take<double>(S);
+  b.nrm = c.take<double>(S);
+  b.kk = c.take<int>(S);
+  if (host_staging) {
+    b.fdev = c.take<cd>((size_t)S * P.Nz * P.nt);
+    b.udev = c.take<cd>((size_t)S * P.Nz * P.nt);
+  }
+  if (bytes) *bytes = c.off;
+  return b;
+}
+
+// ---- operator tables -------------------------------------------------------
+struct TableBuilder {
+  const Plan& P;
+  int tr(int dir, int iface, int ab) const { return dir * P.T + 2 * iface + ab; }
+  static int blk(int l, int jj, int kk) { return l * 16 + jj * 4 + kk; }
+  // G_down_j(p) of layer l, p = top pair (interface l-1): B_{j,1} p.A - B_{j,0} p.B
+  void down(ApplyRow& r, int l, int jj, int inA, int inB, int inA2 = -1, int inB2 = -1) const {
+    r.t[r.nterms++] = ApplyTerm{blk(l, jj, 1), inA, inA2, +1.0};
+    r.t[r.nterms++] = ApplyTerm{blk(l, jj, 0), inB, inB2, -1.0};
+  }
+  // G_up_j(q) of layer l, q = bottom pair (interface l): -B_{j,n+1} q.A + B_{j,n} q.B
+  void up(ApplyRow& r, int l, int jj, int inA, int inB, int inA2 = -1, int inB2 = -1) const {
+    r.t[r.nterms++] = ApplyTerm{blk(l, jj, 3), inA, inA2, -1.0};
+    r.t[r.nterms++] = ApplyTerm{blk(l, jj, 2), inB, inB2, +1.0};
+  }
+  static void ident(ApplyRow& r, int src, int trace, double sign) {
+    r.id_src[r.nid] = src;
+    r.id_trace[r.nid] = trace;
+    r.id_sign[r.nid] = sign;
+    r.nid++;
+  }
+  static ApplyRow row(int out) {
+    ApplyRow r;
+    std::memset(&r, 0, sizeof(r));
+    r.out = out;
+    return r;
+  }
+
+  // y = P M x = (D + R) x: the four jump-condition equations of Section 3.5.
+  std::vector<ApplyRow> matvec() const {
+    std::vector<ApplyRow> v;
+    const int L = P.L;
+    for (int l = 0; l + 1 < L; ++l) {  // down rows of interface l (layer l): j = n, j = n+1
+      for (int jj = 2; jj <= 3; ++jj) {
+        ApplyRow r = row(tr(0, l, jj - 2));
+        if (l >= 1) down(r, l, jj, tr(1, l - 1, 0), tr(1, l - 1, 1), tr(0, l - 1, 0), tr(0, l - 1, 1));
+        up(r, l, jj, tr(1, l, 0), tr(1, l, 1));
+        if (jj == 2) { ident(r, 0, tr(1, l, 0), -1.0); ident(r, 0, tr(0, l, 0), -1.0); }
+        else ident(r, 0, tr(0, l, 1), -1.0);
+        v.push_back(r);
+      }
+    }
+    for (int l = 1; l < L; ++l) {  // up rows of interface l-1 (layer l): j = 0, j = 1
+      for (int jj = 0; jj <= 1; ++jj) {
+        ApplyRow r = row(tr(1, l - 1, jj));
+        down(r, l, jj, tr(0, l - 1, 0), tr(0, l - 1, 1));
+        if (l + 1 < L) up(r, l, jj, tr(1, l, 0), tr(1, l, 1), tr(0, l, 0), tr(0, l, 1));
+        if (jj == 0) ident(r, 0, tr(1, l - 1, 0), -1.0);
+        else { ident(r, 0, tr(1, l - 1, 1), -1.0); ident(r, 0, tr(0, l - 1, 1), -1.0); }
+        v.push_back(r);
+      }
+    }
+    return v;
+  }
+  // y = R x: the couplings between down- and up-going unknowns.
+  std::vector<ApplyRow> coupling() const {
+    std::vector<ApplyRow> v;
+    const int L = P.L;
+    for (int l = 0; l + 1 < L; ++l) {
+      for (int jj = 2; jj <= 3; ++jj) {
+        ApplyRow r = row(tr(0, l, jj - 2));
+        if (l >= 1) down(r, l, jj, tr(1, l - 1, 0), tr(1, l - 1, 1));
+        up(r, l, jj, tr(1, l, 0), tr(1, l, 1));
+        if (jj == 2) ident(r, 0, tr(1, l, 0), -1.0);
+        v.push_back(r);
+      }
+    }
+    for (int l = 1; l < L; ++l) {
+      for (int jj = 0; jj <= 1; ++jj) {
+        ApplyRow r = row(tr(1, l - 1, jj));
+        down(r, l, jj, tr(0, l - 1, 0), tr(0, l - 1, 1));
+        if (l + 1 < L) up(r, l, jj, tr(0, l, 0), tr(0, l, 1));
+        if (jj == 1) ident(r, 0, tr(0, l - 1, 1), -1.0);
+        v.push_back(r);
+      }
+    }
+    return v;
+  }
+  // D^{-1}: step s solves the down-going traces of interface s (top-down
+  // sweep) and the up-going traces of interface L-2-s (bottom-up sweep):
+  //   y_down[l] = T_down^l y_down[l-1] - r_down[l],   y_up[l-1] = T_up^l y_up[l] - r_up[l-1].
+  std::vector<ApplyRow> sweeps() const {
+    std::vector<ApplyRow> v;
+    const int L = P.L;
+    for (int s = 0; s + 1 < L; ++s) {
+      const int l = s;
+      for (int jj = 2; jj <= 3; ++jj) {
+        ApplyRow r = row(tr(0, l, jj - 2));
+        if (l >= 1) down(r, l, jj, tr(0, l - 1, 0), tr(0, l - 1, 1));
+        ident(r, 1, tr(0, l, jj - 2), -1.0);
+        v.push_back(r);
+      }
+      const int lu = L - 1 - s;
+      for (int jj = 0; jj <= 1; ++jj) {
+        ApplyRow r = row(tr(1, lu - 1, jj));
+        if (lu + 1 < L) up(r, lu, jj, tr(1, lu, 0), tr(1, lu, 1));
+        ident(r, 1, tr(1, lu - 1, jj), -1.0);
+        v.push_back(r);
+      }
+    }
+    return v;
+  }
+};
+
+}  // namespace
+
+struct pt_ctx {
+  pt_params prm{};
+  Plan P;
+  Persist d{};
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  int last_max_it = 0;
+  std::vector<double> resid_h;
+};
+
+static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
+                                    "singular local factorization", "GMRES did not converge",
+                                    "device-side wait timed out", "non-finite or non-positive data"};
+
+extern "C" const char* pt_status_string(pt_status s) {
+  int i = (int)s;
+  return (i >= 0 && i < 8) ? kStatusText[i] : "unknown status";
+}
+
+extern "C" const char* pt_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" pt_status pt_layer_partition(const pt_params* prm, int32_t* row_start) {
+  Plan P;
+  pt_status st = make_plan(prm, P);
+  if (st != PT_OK) return st;
+  if (!row_start) return fail(PT_ERR_ARG, "row_start is NULL");
+  for (int l = 0; l < P.L; ++l) row_start[l] = P.layers[l].start;
+  row_start[P.L] = P.Nz;
+  return PT_OK;
+}
+
+extern "C" pt_status pt_workspace_size(const pt_params* prm, size_t* persistent_bytes, size_t* setup_bytes,
+                                       size_t* solve_bytes) {
+  Plan P;
+  pt_status st = make_plan(prm, P);
+  if (st != PT_OK) return st;
+  size_t pb = 0, sb = 0;
+  carve_persist(P, prm, nullptr, &pb);
+  carve_solve(P, prm->max_sources, prm->max_krylov, false, nullptr, &sb);
+  if (persistent_bytes) *persistent_bytes = pb;
+  if (setup_bytes) *setup_bytes = setup_bytes_of(P);
+  if (solve_bytes) *solve_bytes = sb;
+  return PT_OK;
+}
+
+static pt_status read_status(pt_ctx* c) {
+  int st = 0;
+  PT_CUDA(cudaMemcpyAsync(&st, c->d.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (st & kErrNumeric) return fail(PT_ERR_NUMERIC, "non-finite or non-positive value met on the device");
+  if (st & kErrSingular) return fail(PT_ERR_SINGULAR, "zero pivot in a local factorization");
+  if (st & kErrTimeout) return fail(PT_ERR_TIMEOUT, "a device-side wait gave up");
+  return PT_OK;
+}
+
+extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* persistent, size_t persistent_bytes,
+                               void* setup, size_t setup_bytes, void* stream, pt_ctx** out) {
+  if (!out) return fail(PT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  Plan P;
+  pt_status st = make_plan(prm, P);
+  if (st != PT_OK) return st;
+  if (!c_ext || !persistent || !setup) return fail(PT_ERR_ARG, "NULL device pointer");
+  if (((uintptr_t)persistent % kAlign) || ((uintptr_t)setup % kAlign))
+    return fail(PT_ERR_ARG, "workspaces must be 256-byte aligned");
+  size_t need_p = 0;
+  carve_persist(P, prm, nullptr, &need_p);
+  if (persistent_bytes < need_p || setup_bytes < setup_bytes_of(P))
+    return fail(PT_ERR_WORKSPACE, "persistent or setup workspace too small");
+  pt_ctx* c = new (std::nothrow) pt_ctx();
+  if (!c) return fail(PT_ERR_ARG, "host allocation failed");
+  c->prm = *prm;
+  c->P = P;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->d = carve_persist(P, prm, persistent, nullptr);
+  auto bail = [&](pt_status s) { delete c; return s; };
+  cudaStream_t s = c->stream;
+  const Geometry& g = P.g;
+  if (cudaMemsetAsync(c->d.status, 0, 64 * sizeof(int), s) != cudaSuccess ||
+      cudaMemcpyAsync(c->d.layers, P.layers.data(), P.L * sizeof(LayerInfo), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->d.tasks, P.tasks.data(), P.tasks.size() * sizeof(ExtractTask), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    return bail(fail(PT_ERR_CUDA, "copying tables"));
+  TableBuilder tb{P};
+  auto mv = tb.matvec(), rr = tb.coupling(), sw = tb.sweeps();
+  if (cudaMemcpyAsync(c->d.tab_matvec, mv.data(), mv.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->d.tab_R, rr.data(), rr.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->d.tab_sweep, sw.data(), sw.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return bail(fail(PT_ERR_CUDA, "copying operator tables"));
+  // Algorithm 1
+  if (launch_check_medium(c_ext, (size_t)P.Nz * P.nt, c->d.status, s) != cudaSuccess) return bail(fail(PT_ERR_CUDA, "check"));
+  st = read_status(c);
+  if (st != PT_OK) return bail(st);
+  cudaError_t e = launch_coef(g, c->d.layers, c_ext, c->d.W, c->d.E, s);
+  if (e == cudaSuccess) e = launch_factor(g, c->d.layers, P.nloc_max, c_ext, c->d.Sinv, c->d.status, s);
+  const int nslots = std::min<int>((int)P.tasks.size(), kExtractSlots);
+  if (e == cudaSuccess)
+    e = launch_extract(g, c->d.layers, c->d.tasks, (int)P.tasks.size(), nslots, P.nloc_max, c->d.Sinv, c->d.W,
+                       c->d.E, static_cast<cd*>(setup), setup_slot_elems(P), c->d.blocks, s);
+  if (e == cudaSuccess && c->d.blocks32)
+    e = launch_to_fp32(c->d.blocks, c->d.blocks32, (size_t)P.L * 16 * P.nt * P.nt, s);
+  if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline launch: ") + cudaGetErrorString(e)));
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline phase: ") + cudaGetErrorString(e)));
+  st = read_status(c);
+  if (st != PT_OK) return bail(st);
+  *out = c;
+  return PT_OK;
+}
+
+extern "C" void pt_destroy(pt_ctx* ctx) { delete ctx; }
+
+// ---- online building blocks ------------------------------------------------
+namespace {
+
+const void* block_ptr(pt_ctx* c, bool fp32) {
+  return fp32 ? static_cast<const void*>(c->d.blocks32) : static_cast<const void*>(c->d.blocks);
+}
+
+cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y) {
+  c->launches++;
+  return launch_apply(c->P.nt, c->P.T4, c->d.tab_matvec, c->P.T4, false, c->d.blocks, x, nullptr, y, S,
+                      kApplyRowsWide, c->stream);
+}
+
+cudaError_t do_R(pt_ctx* c, int S, const cd* x, cd* y, bool fp32) {
+  c->launches++;
+  return launch_apply(c->P.nt, c->P.T4, c->d.tab_R, c->P.T4, fp32, block_ptr(c, fp32), x, nullptr, y, S,
+                      kApplyRowsWide, c->stream);
+}
+
+// y = D^{-1} r; y must not alias r.
+cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, bool fp32) {
+  const int steps = c->P.L - 1;
+  for (int s = 0; s < steps; ++s) {
+    c->launches++;
+    cudaError_t e = launch_apply(c->P.nt, c->P.T4, c->d.tab_sweep + 4 * s, 4, fp32, block_ptr(c, fp32), y, r, y, S,
+                                 kApplyRowsSweep, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Algorithm 4: u = D^{-1} r; repeat n_it - 1 times u = D^{-1}(r - R u).
+cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* tmp2) {
+  const bool fp32 = c->prm.precision == PT_MIXED_FP32;
+  cudaError_t e = do_Dinv(c, S, r, z, fp32);
+  for (int it = 1; it < c->prm.gs_iters && e == cudaSuccess; ++it) {
+    e = do_R(c, S, z, tmp1, fp32);
+    if (e == cudaSuccess) { c->launches++; e = launch_sub(r, tmp1, tmp2, (size_t)S * c->P.N, c->stream); }
+    if (e == cudaSuccess) e = do_Dinv(c, S, tmp2, z, fp32);
+  }
+  return e;
+}
+
+cudaError_t do_rhs(pt_ctx* c, int S, const cd* f, cd* b, const SolveBufs& B) {
+  c->launches += 2;
+  cudaError_t e = launch_layer_nonzero(c->P.g, c->d.layers, f, B.nzflag, S, c->stream);
+  if (e != cudaSuccess) return e;
+  return launch_layer_solve(0, c->P.g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, f, nullptr, B.Y,
+                            (size_t)c->P.nt * c->P.nloc_max, b, B.nzflag, S, c->stream);
+}
+
+pt_status check_solve_args(pt_ctx* c, int nsrc, void* scratch, size_t scratch_bytes, size_t need) {
+  if (!c) return fail(PT_ERR_ARG, "ctx is NULL");
+  if (nsrc < 1 || nsrc > c->prm.max_sources) return fail(PT_ERR_ARG, "nsrc out of range (1..max_sources)");
+  if (!scratch) return fail(PT_ERR_ARG, "scratch is NULL");
+  if ((uintptr_t)scratch % kAlign) return fail(PT_ERR_ARG, "scratch must be 256-byte aligned");
+  if (scratch_bytes < need) return fail(PT_ERR_WORKSPACE, "scratch too small");
+  return PT_OK;
+}
+
+}  // namespace
+
+extern "C" pt_status pt_apply_matvec(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y) {
+  if (!ctx || !x || !y || nsrc < 1 || nsrc > ctx->prm.max_sources) return fail(PT_ERR_ARG, "bad arguments");
+  PT_CUDA(do_matvec(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y)));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_apply_R(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y) {
+  if (!ctx || !x || !y || nsrc < 1 || nsrc > ctx->prm.max_sources) return fail(PT_ERR_ARG, "bad arguments");
+  PT_CUDA(do_R(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), false));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_apply_D_inverse(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y) {
+  if (!ctx || !x || !y || x == y || nsrc < 1 || nsrc > ctx->prm.max_sources) return fail(PT_ERR_ARG, "bad arguments");
+  PT_CUDA(do_Dinv(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), false));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_apply_precond(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y, void* scratch,
+                                      size_t scratch_bytes) {
+  if (!ctx || !x || !y || x == y) return fail(PT_ERR_ARG, "bad arguments");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  PT_CUDA(do_precond(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), B.t, B.u1));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y, void* scratch,
+                            size_t scratch_bytes) {
+  if (!ctx || !f || !y) return fail(PT_ERR_ARG, "bad arguments");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  PT_CUDA(do_rhs(ctx, nsrc, reinterpret_cast<const cd*>(f), reinterpret_cast<cd*>(y), B));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_get_block(pt_ctx* ctx, int32_t layer, int32_t j, int32_t k, pt_c128* dst) {
+  if (!ctx || !dst || layer < 0 || layer >= ctx->P.L) return fail(PT_ERR_ARG, "bad arguments");
+  const LayerInfo& I = ctx->P.layers[layer];
+  auto idx = [&](int q) -> int {
+    if (I.has_top && q == 0) return 0;
+    if (I.has_top && q == 1) return 1;
+    if (I.has_bot && q == I.n) return 2;
+    if (I.has_bot && q == I.n + 1) return 3;
+    return -1;
+  };
+  int jj = idx(j), kk = idx(k);
+  if (jj < 0 || kk < 0) return fail(PT_ERR_ARG, "j, k must be trace rows of the layer");
+  const size_t bsz = (size_t)ctx->P.nt * ctx->P.nt;
+  PT_CUDA(cudaMemcpyAsync(dst, ctx->d.blocks + ((size_t)layer * 16 + jj * 4 + kk) * bsz, bsz * sizeof(cd),
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_last_solve_stats(const pt_ctx* ctx, int64_t* kernel_launches, int32_t* max_iterations) {
+  if (!ctx) return fail(PT_ERR_ARG, "ctx is NULL");
+  if (kernel_launches) *kernel_launches = ctx->launches;
+  if (max_iterations) *max_iterations = ctx->last_max_it;
+  return PT_OK;
+}
+
+// ---- flexible GMRES (Section 4.2) -------------------------------------------
+static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, double tol, int max_it,
+                            const SolveBufs& B, int32_t* iters_out, double* relres_out) {
+  const Plan& P = c->P;
+  const size_t N = P.N;
+  const int m = c->prm.max_krylov;
+  cudaStream_t s = c->stream;
+  c->launches = 0;
+  std::vector<double> beta(S), rel(S, 1.0);
+  std::vector<int> done(S, 0), kk(S, 0), total(S, 0);
+  c->resid_h.assign(S, 0.0);
+
+  PT_CUDA(cudaMemsetAsync(c->d.status, 0, sizeof(int), s));
+  PT_CUDA(do_rhs(c, S, f, B.b, B));  // P b
+  PT_CUDA(cudaMemsetAsync(B.x, 0, S * N * sizeof(cd), s));
+  // r = P b (x0 = 0)
+  PT_CUDA(cudaMemcpyAsync(B.w, B.b, S * N * sizeof(cd), cudaMemcpyDeviceToDevice, s));
+  bool first = true;
+  int used = 0;
+  std::vector<double> nrm(S);
+  while (true) {
+    // V_0 = r / ||r||, g = (||r||, 0, ...), H = 0
+    PT_CUDA(cudaMemsetAsync(B.H, 0, (size_t)S * (m + 1) * m * sizeof(cd), s));
+    PT_CUDA(cudaMemsetAsync(B.g, 0, (size_t)S * (m + 1) * sizeof(cd), s));
+    c->launches++;
+    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, B.g, 1, m + 1, 0, 0, B.V, N, s));
+    PT_CUDA(cudaMemcpyAsync(nrm.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    if (first) {
+      for (int q = 0; q < S; ++q) {
+        beta[q] = nrm[q];
+        if (beta[q] == 0.0) { done[q] = 1; rel[q] = 0.0; }
+      }
+      first = false;
+    }
+    std::vector<int> active(S, 0);
+    int nact = 0;
+    for (int q = 0; q < S; ++q) {
+      kk[q] = 0;
+      if (!done[q]) { active[q] = 1; nact++; }
+    }
+    if (nact == 0 || used >= max_it) break;
+    int j = 0;
+    for (; j < m && used < max_it; ++j) {
+      cd* Vj = B.V + (size_t)j * S * N;
+      cd* Zj = B.Z + (size_t)j * S * N;
+      PT_CUDA(do_precond(c, S, Vj, Zj, B.t, B.u1));
+      PT_CUDA(do_matvec(c, S, Zj, B.w));
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        c->launches += 3;
+        PT_CUDA(launch_dots(B.V, S, N, B.w, j + 1, B.partial, B.coef, m + 1, B.H, m + 1, m, j, s));
+        PT_CUDA(launch_update(B.V, S, N, B.w, j + 1, B.coef, m + 1, s));
+      }
+      c->launches += 2;
+      PT_CUDA(launch_norm_scale(B.w, N, S, nullptr, B.H, m + 1, m, j + 1, j, B.V + (size_t)(j + 1) * S * N, N, s));
+      PT_CUDA(launch_givens(S, m, j, B.H, B.cs, B.sn, B.g, B.resid, s));
+      PT_CUDA(cudaMemcpyAsync(c->resid_h.data(), B.resid, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+      PT_CUDA(cudaStreamSynchronize(s));
+      used++;
+      bool all = true;
+      for (int q = 0; q < S; ++q) {
+        if (!active[q] || kk[q]) continue;
+        if (!(c->resid_h[q] > tol * beta[q])) kk[q] = j + 1;  // converged (or NaN: stop it too)
+        else all = false;
+      }
+      if (all) { ++j; break; }
+    }
+    for (int q = 0; q < S; ++q) {
+      if (active[q] && !kk[q]) kk[q] = j;
+      total[q] += active[q] ? kk[q] : 0;
+    }
+    PT_CUDA(cudaMemcpyAsync(B.kk, kk.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+    c->launches += 2;
+    PT_CUDA(launch_lsq_combine(S, m, B.kk, B.H, B.g, B.y, B.Z, N, B.x, s));
+    // explicit residual r = P b - P M x
+    PT_CUDA(do_matvec(c, S, B.x, B.t));
+    c->launches += 2;
+    PT_CUDA(launch_sub(B.b, B.t, B.w, S * N, s));
+    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, s));
+    PT_CUDA(cudaMemcpyAsync(nrm.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int q = 0; q < S; ++q) {
+      if (done[q]) continue;
+      rel[q] = nrm[q] / beta[q];
+      if (rel[q] <= tol) done[q] = 1;
+      else all = false;
+    }
+    if (all || used >= max_it) break;
+  }
+  // outputs
+  if (traces) PT_CUDA(cudaMemcpyAsync(traces, B.x, S * N * sizeof(cd), cudaMemcpyDeviceToDevice, s));
+  if (u) {
+    c->launches++;
+    PT_CUDA(launch_layer_solve(1, P.g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, f, B.x, B.Y,
+                               (size_t)P.nt * P.nloc_max, u, B.nzflag, S, s));
+  }
+  PT_CUDA(cudaStreamSynchronize(s));
+  pt_status st = read_status(c);
+  if (st != PT_OK) return st;
+  int maxit = 0;
+  bool conv = true;
+  for (int q = 0; q < S; ++q) {
+    if (iters_out) iters_out[q] = total[q];
+    if (relres_out) relres_out[q] = rel[q];
+    maxit = std::max(maxit, total[q]);
+    if (!(rel[q] <= tol)) conv = false;
+  }
+  c->last_max_it = maxit;
+  if (!conv) return fail(PT_ERR_NOT_CONVERGED, "GMRES reached max_it before rel_tol");
+  return PT_OK;
+}
+
+extern "C" pt_status pt_solve(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* u, pt_c128* traces,
+                              double rel_tol, int32_t max_it, void* scratch, size_t scratch_bytes, int32_t* iters,
+                              double* relres) {
+  if (!ctx || !f) return fail(PT_ERR_ARG, "ctx or f is NULL");
+  if (!(rel_tol > 0) || max_it < 1) return fail(PT_ERR_ARG, "rel_tol > 0 and max_it >= 1 required");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  return solve_impl(ctx, nsrc, reinterpret_cast<const cd*>(f), reinterpret_cast<cd*>(u),
+                    reinterpret_cast<cd*>(traces), rel_tol, max_it, B, iters, relres);
+}
+
+extern "C" pt_status pt_solve_host(pt_ctx* ctx, int32_t nsrc, const pt_c128* f_host, pt_c128* u_host,
+                                   double rel_tol, int32_t max_it, void* scratch, size_t scratch_bytes,
+                                   int32_t* iters, double* relres) {
+  if (!ctx || !f_host || !u_host) return fail(PT_ERR_ARG, "NULL pointer");
+  if (!(rel_tol > 0) || max_it < 1) return fail(PT_ERR_ARG, "rel_tol > 0 and max_it >= 1 required");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, true, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, true, scratch, nullptr);
+  const size_t vol = (size_t)nsrc * ctx->P.Nz * ctx->P.nt * sizeof(cd);
+  PT_CUDA(cudaMemcpyAsync(B.fdev, f_host, vol, cudaMemcpyHostToDevice, ctx->stream));
+  st = solve_impl(ctx, nsrc, B.fdev, B.udev, nullptr, rel_tol, max_it, B, iters, relres);
+  if (st != PT_OK && st != PT_ERR_NOT_CONVERGED) return st;
+  PT_CUDA(cudaMemcpyAsync(u_host, B.udev, vol, cudaMemcpyDeviceToHost, ctx->stream));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return st;
+}

@@ -1,0 +1,98 @@
+"""The C-ABI library loads and exports every symbol include/polartrace.h declares (CPU only).
+
+Also checks the host-only entry points (partition, workspace sizes, argument
+validation) that need no GPU.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import discretization as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "polartrace.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1410_5910_gb300 import _lib
+    from paper_1410_5910_gb300.build import LIB, build
+
+    if not os.path.exists(LIB):
+        build()
+    return _lib.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pt_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_1410_5910_gb300 import _lib
+
+    assert sorted(_lib.EXPORTS) == names
+
+
+def test_symbols_in_shared_object_are_c_linkage():
+    from paper_1410_5910_gb300.build import LIB
+
+    if not os.path.exists(LIB):
+        pytest.skip("library not built")
+    import subprocess
+
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (pt_\w+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+
+
+def _params(L_, **kw):
+    from paper_1410_5910_gb300._lib import Params
+
+    d = dict(nx=128, nz=128, npml=10, L=4, h=1 / 129, omega=81.0, pml_C=20.0, precision=0, gs_iters=2,
+             max_sources=1, max_krylov=30)
+    d.update(kw)
+    return Params(**d)
+
+
+@pytest.mark.parametrize("nz,npml,L_", [(128, 10, 4), (1023, 20, 16), (2047, 20, 32), (100, 7, 3)])
+def test_partition_matches_oracle(L, nz, npml, L_):
+    p = _params(L, nz=nz, npml=npml, L=L_)
+    out = (C.c_int32 * (L_ + 1))()
+    assert L.pt_layer_partition(C.byref(p), out) == 0
+    assert list(out) == list(D.layer_partition(nz + 2 * npml, L_))
+
+
+def test_workspace_sizes_and_validation(L):
+    p = _params(L)
+    a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    assert L.pt_workspace_size(C.byref(p), C.byref(a), C.byref(b), C.byref(c)) == 0
+    nt, L_ = 148, 4
+    # at least the Green's blocks in FP64 and the local factors
+    assert a.value >= L_ * 16 * nt * nt * 16
+    p2 = _params(L, precision=1)
+    a2 = C.c_size_t()
+    assert L.pt_workspace_size(C.byref(p2), C.byref(a2), None, None) == 0
+    assert a2.value > a.value  # FP32 copies of the blocks
+    for bad in (dict(L=1), dict(h=0.0), dict(omega=-1.0), dict(gs_iters=0), dict(L=70), dict(npml=0),
+                dict(precision=7), dict(max_krylov=0)):
+        assert L.pt_workspace_size(C.byref(_params(L, **bad)), None, None, None) == 1, bad
+    assert b"" != L.pt_last_error()
+    assert L.pt_status_string(5) == b"GMRES did not converge"
+
+
+def test_create_rejects_null_and_small_workspace_without_touching_the_gpu(L):
+    p = _params(L)
+    ctx = C.c_void_p()
+    assert L.pt_create(C.byref(p), None, None, 0, None, 0, None, C.byref(ctx)) == 1
+    assert L.pt_create(C.byref(p), C.c_void_p(256), C.c_void_p(256), 16, C.c_void_p(512), 16, None,
+                       C.byref(ctx)) == 2
+    assert not ctx.value
