@@ -156,6 +156,32 @@ pt_status pt_apply_D_inverse(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c12
 pt_status pt_apply_R(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y);
 pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y, void* scratch, size_t scratch_bytes);
 
+/* pt_rhs_noalloc: the same result as pt_rhs (y = P b for nsrc sources; f and
+ * y device, same layouts) for callers that cannot allocate device memory at
+ * all, not even the scratch buffer that pt_rhs takes as an argument.  Such
+ * callers are, for example, code running inside a host framework whose pool
+ * owns every device allocation and hands out none, or a serving loop that
+ * must not call cudaMalloc after start-up because the call can synchronise
+ * the device and stall work on other streams.  The paper has no counterpart:
+ * this is an interface convenience, not part of the method.
+ *   Scratch: the local-solve storage lives in one 16 MiB array in the
+ *   library's own device memory (loaded with the library, held by every GPU
+ *   that loads it until the process exits).  A call needs
+ *   nsrc * L * n_t * nloc_max * 16 bytes (rounded up to 256) plus
+ *   nsrc * L * 4 bytes, nloc_max = the largest layer height + 2 n_pml;
+ *   larger requests fail with PT_ERR_WORKSPACE and nothing is launched
+ *   (use pt_rhs then).  No call allocates (no cudaMalloc, cudaFree or any
+ *   allocating library routine).
+ *   Set-up: the first call on a device, with that device current, looks up
+ *   the array's device address once (cudaGetSymbolAddress) and caches it;
+ *   make that first call before any stream capture.  The device current at
+ *   every call must be the one the context was created on.
+ *   Sharing: every call uses the same array and leaves its contents behind;
+ *   a call writes every byte it reads, so nothing needs clearing, but calls
+ *   that overlap on the GPU (other streams, other threads) race on the array.
+ *   The call returns after its work on the context's stream has finished. */
+pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y);
+
 /* Copy the interface Green's matrix G^l(z_j, z_k) / h (the block that the
  * incomplete Green's integrals of Definition 2 multiply) to dst (device,
  * n_t * n_t pt_c128, row-major, row = target node, column = source node).

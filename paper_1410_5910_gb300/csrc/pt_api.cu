@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -728,4 +729,59 @@ extern "C" pt_status pt_solve_host(pt_ctx* ctx, int32_t nsrc, const pt_c128* f_h
   PT_CUDA(cudaMemcpyAsync(u_host, B.udev, vol, cudaMemcpyDeviceToHost, ctx->stream));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return st;
+}
+
+// ---- pt_rhs_noalloc: pt_rhs without caller-provided scratch -----------------
+// The local-solve storage of pt_rhs, for callers that cannot allocate device
+// memory, lives in this file-scope device array.  Host code must not use the
+// name g_rhs_noalloc_scratch as an address (on the host it only stands for
+// the symbol); its device address is looked up once per device below.
+namespace {
+constexpr size_t kRhsNoallocBytes = 16u << 20;  // 16 MiB
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_rhs_noalloc_scratch[kRhsNoallocBytes];
+
+// Device address of the array on the current device; the first call on a
+// device performs the lookup (cudaGetSymbolAddress) with that device current.
+static pt_status rhs_noalloc_scratch(void** out) {
+  int dev = -1;
+  PT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(PT_ERR_ARG, "pt_rhs_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_rhs_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(PT_ERR_CUDA, std::string("pt_rhs_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return PT_OK;
+}
+
+extern "C" pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y) {
+  if (!ctx || !f || !y) return fail(PT_ERR_ARG, "pt_rhs_noalloc: NULL argument");
+  if (nsrc < 1) return fail(PT_ERR_ARG, "pt_rhs_noalloc: nsrc must be >= 1");
+  const Plan& P = ctx->P;
+  const size_t ystride = (size_t)P.nt * P.nloc_max;
+  const size_t ybytes = ((size_t)nsrc * P.L * ystride * sizeof(cd) + kAlign - 1) / kAlign * kAlign;
+  const size_t need = ybytes + (size_t)nsrc * P.L * sizeof(int);
+  if (need > kRhsNoallocBytes)
+    return fail(PT_ERR_WORKSPACE, "pt_rhs_noalloc: needs " + std::to_string(need) +
+                                      " bytes, more than its 16 MiB built-in scratch; use pt_rhs");
+  void* base = nullptr;
+  pt_status st = rhs_noalloc_scratch(&base);
+  if (st != PT_OK) return st;
+  cd* Y = static_cast<cd*>(base);
+  int* flag = reinterpret_cast<int*>(static_cast<char*>(base) + ybytes);
+  const cd* fd = reinterpret_cast<const cd*>(f);
+  PT_CUDA(launch_layer_nonzero(P.g, ctx->d.layers, fd, flag, nsrc, ctx->stream));
+  PT_CUDA(launch_layer_solve(0, P.g, ctx->d.layers, ctx->d.Sinv, ctx->d.W, ctx->d.E, fd, nullptr, Y, ystride,
+                             reinterpret_cast<cd*>(y), flag, nsrc, ctx->stream));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
 }
