@@ -24,12 +24,19 @@ cudaError_t launch_coef(const Geometry&, const LayerInfo*, const double*, cd*, c
 cudaError_t launch_factor(const Geometry&, const LayerInfo*, int, const double*, cd*, int*, cudaStream_t);
 cudaError_t launch_extract(const Geometry&, const LayerInfo*, const ExtractTask*, int, int, int, const cd*,
                            const cd*, const cd*, cd*, size_t, cd*, cudaStream_t);
-cudaError_t launch_to_fp32(const cd*, cf*, size_t, cudaStream_t);
-cudaError_t launch_apply(int, int, const ApplyRow*, int, bool, const void*, const cd*, const cd*, cd*, int, int,
-                         cudaStream_t);
+cudaError_t launch_apply_mode(int, int, int, int, const ApplyRow*, int, const void*, const void*, const cd*,
+                              const cd*, cd*, int, int, double, double, cudaStream_t);
+cudaError_t launch_split_blocks(const cd*, int, int, size_t, cf*, cf*, cudaStream_t);
+cudaError_t launch_split_sinv(const cd*, size_t, cf*, cf*, cudaStream_t);
 cudaError_t launch_layer_nonzero(const Geometry&, const LayerInfo*, const cd*, int*, int, cudaStream_t);
 cudaError_t launch_layer_solve(int, const Geometry&, const LayerInfo*, const cd*, const cd*, const cd*, const cd*,
                                const cd*, cd*, size_t, cd*, const int*, int, cudaStream_t);
+cudaError_t launch_layer_solve2(int, bool, const Geometry&, const LayerInfo*, const cd*, const cf*, const cf*,
+                                const cd*, const cd*, const cd*, const cd*, cd*, size_t, cd*, const int*, int,
+                                cudaStream_t);
+cudaError_t launch_layer_solve_df(int, const Geometry&, const LayerInfo*, const cf*, const cf*, const cf*, const cf*,
+                                  const cf*, const cf*, const cd*, const cd*, cd*, size_t, cd*, const int*, int,
+                                  cudaStream_t);
 int dot_chunks(size_t N);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
@@ -79,6 +86,7 @@ struct Carver {
 struct Plan {
   Geometry g{};
   int L = 0, nt = 0, Nz = 0, T = 0, T4 = 0;
+  int ld32 = 0;  // row stride of the FP32 block copies (n_t rounded up to 4: 16-byte aligned rows)
   size_t N = 0;  // entries of one polarized-trace vector
   int nloc_max = 0;
   std::vector<LayerInfo> layers;
@@ -103,6 +111,7 @@ pt_status make_plan(const pt_params* p, Plan& P) {
   P.T = 2 * (P.L - 1);
   P.T4 = 4 * (P.L - 1);
   P.N = (size_t)P.T4 * P.nt;
+  P.ld32 = (P.nt + 3) & ~3;
   P.g = Geometry{P.nt, P.Nz, p->npml, P.L, p->h, p->omega, p->pml_C};
   // near-equal split: the first (N_z mod L) layers get one extra row
   const int base = P.Nz / P.L, extra = P.Nz % P.L;
@@ -156,7 +165,11 @@ struct Persist {
   cd* E;
   cd* Sinv;
   cd* blocks;
-  cf* blocks32;
+  cf* blocks_hi;  // mixed form: fl32(B) and fl32(B - hi), rows padded to ld32
+  cf* blocks_lo;
+  cf* sinv_hi;    // mixed form: double-float split of the local factors
+  cf* sinv_lo;
+  cf *w_hi, *w_lo, *e_hi, *e_lo;  // mixed form: double-float split of the x-couplings
   ApplyRow* tab_matvec;
   ApplyRow* tab_R;
   ApplyRow* tab_sweep;
@@ -173,7 +186,17 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
   q.Sinv = c.take<cd>(P.sinv_elems);
   const size_t bel = (size_t)P.L * 16 * P.nt * P.nt;
   q.blocks = c.take<cd>(bel);
-  q.blocks32 = p->precision == PT_MIXED_FP32 ? c.take<cf>(bel) : nullptr;
+  if (p->precision == PT_MIXED_FP32) {
+    const size_t bel32 = (size_t)P.L * 16 * P.nt * P.ld32;
+    q.blocks_hi = c.take<cf>(bel32);
+    q.blocks_lo = c.take<cf>(bel32);
+    q.sinv_hi = c.take<cf>(P.sinv_elems);
+    q.sinv_lo = c.take<cf>(P.sinv_elems);
+    q.w_hi = c.take<cf>(P.coef_elems);
+    q.w_lo = c.take<cf>(P.coef_elems);
+    q.e_hi = c.take<cf>(P.coef_elems);
+    q.e_lo = c.take<cf>(P.coef_elems);
+  }
   q.tab_matvec = c.take<ApplyRow>(P.T4);
   q.tab_R = c.take<ApplyRow>(P.T4);
   q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
@@ -437,8 +460,11 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   if (e == cudaSuccess)
     e = launch_extract(g, c->d.layers, c->d.tasks, (int)P.tasks.size(), nslots, P.nloc_max, c->d.Sinv, c->d.W,
                        c->d.E, static_cast<cd*>(setup), setup_slot_elems(P), c->d.blocks, s);
-  if (e == cudaSuccess && c->d.blocks32)
-    e = launch_to_fp32(c->d.blocks, c->d.blocks32, (size_t)P.L * 16 * P.nt * P.nt, s);
+  if (e == cudaSuccess && c->d.blocks_hi)
+    e = launch_split_blocks(c->d.blocks, P.nt, P.ld32, (size_t)P.L * 16 * P.nt, c->d.blocks_hi, c->d.blocks_lo, s);
+  if (e == cudaSuccess && c->d.sinv_hi) e = launch_split_sinv(c->d.Sinv, P.sinv_elems, c->d.sinv_hi, c->d.sinv_lo, s);
+  if (e == cudaSuccess && c->d.w_hi) e = launch_split_sinv(c->d.W, P.coef_elems, c->d.w_hi, c->d.w_lo, s);
+  if (e == cudaSuccess && c->d.e_hi) e = launch_split_sinv(c->d.E, P.coef_elems, c->d.e_hi, c->d.e_lo, s);
   if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline launch: ") + cudaGetErrorString(e)));
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline phase: ") + cudaGetErrorString(e)));
@@ -453,52 +479,71 @@ extern "C" void pt_destroy(pt_ctx* ctx) { delete ctx; }
 // ---- online building blocks ------------------------------------------------
 namespace {
 
-const void* block_ptr(pt_ctx* c, bool fp32) {
-  return fp32 ? static_cast<const void*>(c->d.blocks32) : static_cast<const void*>(c->d.blocks);
-}
+enum { kModeFP64 = 0, kModeFP32 = 1, kModeDF = 2 };
 
-cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y) {
+bool mixed(const pt_ctx* c) { return c->prm.precision == PT_MIXED_FP32; }
+
+cudaError_t apply(pt_ctx* c, int mode, const ApplyRow* table, int nrows, int S, const cd* x, const cd* aux, cd* y,
+                  int rows_per_cta, double alpha, double beta) {
   c->launches++;
-  return launch_apply(c->P.nt, c->P.T4, c->d.tab_matvec, c->P.T4, false, c->d.blocks, x, nullptr, y, S,
-                      kApplyRowsWide, c->stream);
+  const Plan& P = c->P;
+  if (mode == kModeFP64)
+    return launch_apply_mode(kModeFP64, P.nt, P.nt, P.T4, table, nrows, c->d.blocks, nullptr, x, aux, y, S,
+                             rows_per_cta, alpha, beta, c->stream);
+  return launch_apply_mode(mode, P.nt, P.ld32, P.T4, table, nrows, c->d.blocks_hi, c->d.blocks_lo, x, aux, y, S,
+                           rows_per_cta, alpha, beta, c->stream);
 }
 
-cudaError_t do_R(pt_ctx* c, int S, const cd* x, cd* y, bool fp32) {
-  c->launches++;
-  return launch_apply(c->P.nt, c->P.T4, c->d.tab_R, c->P.T4, fp32, block_ptr(c, fp32), x, nullptr, y, S,
-                      kApplyRowsWide, c->stream);
+// y = P M x.  exact: FP64 blocks (true residual); otherwise the context's
+// working precision (double-float in the mixed form).
+cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y, bool exact = true) {
+  const int mode = (exact || !mixed(c)) ? kModeFP64 : kModeDF;
+  return apply(c, mode, c->d.tab_matvec, c->P.T4, S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0);
 }
 
-// y = D^{-1} r; y must not alias r.
-cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, bool fp32) {
+// y = alpha R x + beta aux
+cudaError_t do_R(pt_ctx* c, int S, const cd* x, cd* y, int mode, double alpha = 1.0, double beta = 0.0,
+                 const cd* aux = nullptr) {
+  return apply(c, mode, c->d.tab_R, c->P.T4, S, x, aux, y, kApplyRowsWide, alpha, beta);
+}
+
+// y = D^{-1} r (one launch per sweep step, down and up sweeps together); y must not alias r.
+cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode) {
   const int steps = c->P.L - 1;
   for (int s = 0; s < steps; ++s) {
-    c->launches++;
-    cudaError_t e = launch_apply(c->P.nt, c->P.T4, c->d.tab_sweep + 4 * s, 4, fp32, block_ptr(c, fp32), y, r, y, S,
-                                 kApplyRowsSweep, c->stream);
+    cudaError_t e = apply(c, mode, c->d.tab_sweep + 4 * s, 4, S, y, r, y, kApplyRowsSweep, 1.0, 0.0);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// Algorithm 4: u = D^{-1} r; repeat n_it - 1 times u = D^{-1}(r - R u).
-cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* tmp2) {
-  const bool fp32 = c->prm.precision == PT_MIXED_FP32;
-  cudaError_t e = do_Dinv(c, S, r, z, fp32);
+// Algorithm 4: z = D^{-1} r; repeat n_it - 1 times z = D^{-1}(r - R z).
+// Mixed form: FP32 blocks (the preconditioner only has to be approximate in flexible GMRES).
+cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* /*tmp2*/) {
+  const int mode = mixed(c) ? kModeFP32 : kModeFP64;
+  cudaError_t e = do_Dinv(c, S, r, z, mode);
   for (int it = 1; it < c->prm.gs_iters && e == cudaSuccess; ++it) {
-    e = do_R(c, S, z, tmp1, fp32);
-    if (e == cudaSuccess) { c->launches++; e = launch_sub(r, tmp1, tmp2, (size_t)S * c->P.N, c->stream); }
-    if (e == cudaSuccess) e = do_Dinv(c, S, tmp2, z, fp32);
+    e = do_R(c, S, z, tmp1, mode, -1.0, 1.0, r);  // tmp1 = r - R z
+    if (e == cudaSuccess) e = do_Dinv(c, S, tmp1, z, mode);
   }
   return e;
 }
 
+cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xtr, cd* out, const SolveBufs& B) {
+  c->launches++;
+  const Plan& P = c->P;
+  if (mixed(c))
+    return launch_layer_solve_df(mode, P.g, c->d.layers, c->d.sinv_hi, c->d.sinv_lo, c->d.w_hi, c->d.w_lo, c->d.e_hi,
+                                 c->d.e_lo, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
+  return launch_layer_solve2(mode, false, P.g, c->d.layers, c->d.Sinv, nullptr, nullptr, c->d.W, c->d.E, f, xtr,
+                             B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
+}
+
 cudaError_t do_rhs(pt_ctx* c, int S, const cd* f, cd* b, const SolveBufs& B) {
-  c->launches += 2;
+  c->launches++;
   cudaError_t e = launch_layer_nonzero(c->P.g, c->d.layers, f, B.nzflag, S, c->stream);
   if (e != cudaSuccess) return e;
-  return launch_layer_solve(0, c->P.g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, f, nullptr, B.Y,
-                            (size_t)c->P.nt * c->P.nloc_max, b, B.nzflag, S, c->stream);
+  return do_layer_solve(c, 0, S, f, nullptr, b, B);
 }
 
 pt_status check_solve_args(pt_ctx* c, int nsrc, void* scratch, size_t scratch_bytes, size_t need) {
@@ -521,14 +566,14 @@ extern "C" pt_status pt_apply_matvec(pt_ctx* ctx, int32_t nsrc, const pt_c128* x
 
 extern "C" pt_status pt_apply_R(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y) {
   if (!ctx || !x || !y || nsrc < 1 || nsrc > ctx->prm.max_sources) return fail(PT_ERR_ARG, "bad arguments");
-  PT_CUDA(do_R(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), false));
+  PT_CUDA(do_R(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), kModeFP64));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
 }
 
 extern "C" pt_status pt_apply_D_inverse(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y) {
   if (!ctx || !x || !y || x == y || nsrc < 1 || nsrc > ctx->prm.max_sources) return fail(PT_ERR_ARG, "bad arguments");
-  PT_CUDA(do_Dinv(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), false));
+  PT_CUDA(do_Dinv(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), kModeFP64));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
 }
@@ -554,7 +599,11 @@ extern "C" pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128
   pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
   if (st != PT_OK) return st;
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
-  PT_CUDA(do_rhs(ctx, nsrc, reinterpret_cast<const cd*>(f), reinterpret_cast<cd*>(y), B));
+  const cd* fd = reinterpret_cast<const cd*>(f);
+  PT_CUDA(launch_layer_nonzero(ctx->P.g, ctx->d.layers, fd, B.nzflag, nsrc, ctx->stream));
+  PT_CUDA(launch_layer_solve(0, ctx->P.g, ctx->d.layers, ctx->d.Sinv, ctx->d.W, ctx->d.E, fd, nullptr, B.Y,
+                             (size_t)ctx->P.nt * ctx->P.nloc_max, reinterpret_cast<cd*>(y), B.nzflag, nsrc,
+                             ctx->stream));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
 }
@@ -632,7 +681,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
       cd* Vj = B.V + (size_t)j * S * N;
       cd* Zj = B.Z + (size_t)j * S * N;
       PT_CUDA(do_precond(c, S, Vj, Zj, B.t, B.u1));
-      PT_CUDA(do_matvec(c, S, Zj, B.w));
+      PT_CUDA(do_matvec(c, S, Zj, B.w, /*exact=*/false));
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         c->launches += 3;
         PT_CUDA(launch_dots(B.V, S, N, B.w, j + 1, B.partial, B.coef, m + 1, B.H, m + 1, m, j, s));
@@ -677,11 +726,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
   }
   // outputs
   if (traces) PT_CUDA(cudaMemcpyAsync(traces, B.x, S * N * sizeof(cd), cudaMemcpyDeviceToDevice, s));
-  if (u) {
-    c->launches++;
-    PT_CUDA(launch_layer_solve(1, P.g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, f, B.x, B.Y,
-                               (size_t)P.nt * P.nloc_max, u, B.nzflag, S, s));
-  }
+  if (u) PT_CUDA(do_layer_solve(c, 1, S, f, B.x, u, B));
   PT_CUDA(cudaStreamSynchronize(s));
   pt_status st = read_status(c);
   if (st != PT_OK) return st;

@@ -273,13 +273,6 @@ __global__ void __launch_bounds__(256) extract_kernel(Geometry g, const LayerInf
   }
 }
 
-__global__ void to_fp32_kernel(const cd* __restrict__ src, cf* __restrict__ dst, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    cd v = src[k];
-    dst[k] = make_float2((float)v.x, (float)v.y);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
@@ -312,9 +305,5 @@ cudaError_t launch_extract(const Geometry& g, const LayerInfo* layers, const Ext
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_fp32(const cd* src, cf* dst, size_t n, cudaStream_t s) {
-  to_fp32_kernel<<<608, 256, 0, s>>>(src, dst, n);
-  return cudaGetLastError();
-}
 
 }  // namespace pt

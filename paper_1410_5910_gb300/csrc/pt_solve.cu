@@ -1,0 +1,589 @@
+// Local solves (H^l)^{-1} (Algorithm 2, "solve local problems" and the
+// reconstruction of Section 2.3) with the block factorization of the offline
+// phase: forward  y_i = Sinv_i (f_i - W_i o y_{i-1}),
+//         backward x_i = y_i - Sinv_i (E_i o x_{i+1}),   i = 0 .. n_t - 1,
+// a chain of 2 n_t - 1 dependent nloc x nloc products.
+//
+// One thread-block cluster of kSolveCS CTAs per (layer, source): each CTA
+// owns a slice of the nloc rows, computes its part of each product and
+// stores it into every CTA's shared memory (distributed shared memory); one
+// cluster barrier per step.  All global loads of step i+1 (Sinv entries,
+// couplings, source / forcing values, stored forward iterates) are issued
+// during step i, so the serial path holds only shared-memory traffic, the
+// arithmetic and the barrier.
+//
+// Arithmetic: FP64 (layer_solve_kernel), or double-float
+// (layer_solve_df_kernel below: Sinv stored as FP32 hi + lo, products and
+// sums in FP32 pairs with error-free transformations, ~2^-45 relative), which
+// moves the products off GB300's FP64 pipe.
+#include <cooperative_groups.h>
+
+#include "pt_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pt {
+
+constexpr int kSolveCS = 8;                                              // CTAs per cluster
+constexpr int kSolveRowsPerCta = (kMaxNloc + kSolveCS - 1) / kSolveCS;  // 15
+constexpr int kSolveRW = (kSolveRowsPerCta + 7) / 8;                     // rows per warp: 2
+constexpr int kSolveCW = (kMaxNloc + 31) / 32;                           // columns per lane: 4
+
+__device__ __forceinline__ void ts(float a, float b, float& s, float& e) {
+  s = a + b;
+  float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+__device__ __forceinline__ void dfmac(float ah, float al, float xh, float xl, float& S, float& C) {
+  float p = ah * xh;
+  float pe = fmaf(ah, xh, -p);
+  float s, e;
+  ts(S, p, s, e);
+  S = s;
+  C += e + pe;
+  C = fmaf(ah, xl, C);
+  C = fmaf(al, xh, C);
+}
+__device__ __forceinline__ void df_shfl(float& S, float& C, int off) {
+  float S2 = __shfl_down_sync(0xffffffffu, S, off);
+  float C2 = __shfl_down_sync(0xffffffffu, C, off);
+  float s, e;
+  ts(S, S2, s, e);
+  S = s;
+  C = C + C2 + e;
+}
+
+// MODE 0: right-hand side, out = P b (trace vector), b = (-f, -f_0):
+//   down rows of interface l: -N^l_n f, -N^l_{n+1} f; up rows of interface l-1: -N^l_0 f, -N^l_1 f.
+// MODE 1: reconstruction, out = volume field; forcing f^l + (1/h^2)(row 1: +u_0,
+//   row 0: -u_1, row n+1: -u_n, row n: +u_{n+1}) with u = u_down + u_up read from xtr.
+template <int MODE, bool DF>
+__global__ void __cluster_dims__(kSolveCS, 1, 1) __launch_bounds__(256)
+    layer_solve_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cd* __restrict__ Sinv,
+                       const cf* __restrict__ Shi, const cf* __restrict__ Slo, const cd* __restrict__ W,
+                       const cd* __restrict__ E, const cd* __restrict__ f, const cd* __restrict__ xtr,
+                       cd* __restrict__ Ystore, size_t ystride, cd* __restrict__ out, const int* __restrict__ nzflag) {
+  __shared__ __align__(16) cd ybuf[2][kMaxNloc];
+  __shared__ __align__(16) float4 vloc[kMaxNloc];  // FP64 mode: (re, im) as a double2 in the same 16 bytes
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int l = blockIdx.x / kSolveCS;
+  const int s = blockIdx.y;
+  const LayerInfo L = layers[l];
+  const int n = L.nloc, nt = g.nt;
+  const int T = 2 * (g.L - 1);
+  const size_t T4n = (size_t)2 * T * nt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpc = (n + kSolveCS - 1) / kSolveCS;
+  const int r0 = rank * rpc, r1 = min(n, r0 + rpc);
+
+  if (MODE == 0 && nzflag[s * g.L + l] == 0) {
+    // f^l = 0: the local potentials vanish
+    cd* b = out + (size_t)s * T4n;
+    for (int k = rank * blockDim.x + threadIdx.x; k < nt; k += kSolveCS * blockDim.x) {
+      if (L.has_bot) {
+        b[(size_t)(2 * l) * nt + k] = make_double2(0, 0);
+        b[(size_t)(2 * l + 1) * nt + k] = make_double2(0, 0);
+      }
+      if (L.has_top) {
+        b[(size_t)(T + 2 * (l - 1)) * nt + k] = make_double2(0, 0);
+        b[(size_t)(T + 2 * (l - 1) + 1) * nt + k] = make_double2(0, 0);
+      }
+    }
+    return;  // uniform over the cluster, before any cluster barrier
+  }
+
+  const cd* fs = f + (size_t)s * g.Nz * nt;
+  const cd* xs = (MODE == 1) ? xtr + (size_t)s * T4n : nullptr;
+  cd* Y = Ystore + ((size_t)s * g.L + l) * ystride;
+  const double ih2 = 1.0 / (g.h * g.h);
+  const int nsteps = 2 * nt - 1;
+  auto step_col = [&](int st) { return st < nt ? st : (nt - 2 - (st - nt)); };
+
+  // ---- the role of this thread in the right-hand-side update: row rv = threadIdx.x
+  const int rv = threadIdx.x;
+  const bool vrow = rv < n;
+  const bool in_layer = vrow && rv >= L.pad_top && rv < L.pad_top + L.n;
+  const size_t frow = in_layer ? (size_t)(L.start + rv - L.pad_top) * nt : 0;
+  // forcing of the reconstruction on the four trace rows: trace index and sign
+  int ftr = -1;
+  double fsg = 0.0;
+  if (MODE == 1 && vrow) {
+    if (L.has_top && rv == L.row[1]) { ftr = 2 * (l - 1); fsg = ih2; }
+    if (L.has_top && rv == L.row[0]) { ftr = 2 * (l - 1) + 1; fsg = -ih2; }
+    if (L.has_bot && rv == L.row[3]) { ftr = 2 * l; fsg = -ih2; }
+    if (L.has_bot && rv == L.row[2]) { ftr = 2 * l + 1; fsg = ih2; }
+  }
+
+  // Prefetched operands of the next step.  Every load below is predicated
+  // and its result is not selected against anything, so the thread does not
+  // wait for it until the next step reads the register; predicates that are
+  // false for a thread at every step leave the register at zero.
+  cd p_sinv[kSolveRW][kSolveCW];
+  cf p_hi[kSolveRW][kSolveCW], p_lo[kSolveRW][kSolveCW];
+#pragma unroll
+  for (int a = 0; a < kSolveRW; ++a)
+#pragma unroll
+    for (int c = 0; c < kSolveCW; ++c) {
+      p_sinv[a][c] = make_double2(0, 0);
+      p_hi[a][c] = make_float2(0.f, 0.f);
+      p_lo[a][c] = make_float2(0.f, 0.f);
+    }
+  cd p_coef = make_double2(0, 0), p_f = make_double2(0, 0), p_ta = make_double2(0, 0), p_tb = make_double2(0, 0);
+  cd p_y[kSolveRW];
+#pragma unroll
+  for (int a = 0; a < kSolveRW; ++a) p_y[a] = make_double2(0, 0);
+
+  auto fetch = [&](int st) {
+    const int i = step_col(st);
+    const bool fwd = st < nt;
+    const size_t base = L.sinv_off + (size_t)i * n * n;
+#pragma unroll
+    for (int a = 0; a < kSolveRW; ++a) {
+      const int r = r0 + warp + 8 * a;
+#pragma unroll
+      for (int c = 0; c < kSolveCW; ++c) {
+        const int k = lane + 32 * c;
+        if (r < r1 && k < n) {
+          if (DF) {
+            p_hi[a][c] = __ldg(Shi + base + (size_t)r * n + k);
+            p_lo[a][c] = __ldg(Slo + base + (size_t)r * n + k);
+          } else {
+            p_sinv[a][c] = __ldg(Sinv + base + (size_t)r * n + k);
+          }
+        }
+      }
+      if (!fwd && lane == 0 && r < r1) p_y[a] = Y[(size_t)i * n + r];
+    }
+    if (vrow) {
+      const cd* cp = (fwd ? W : E) + L.coef_off + (size_t)i * n + rv;
+      p_coef = __ldg(cp);
+      if (fwd && in_layer) p_f = fs[frow + i];
+      if (MODE == 1 && fwd && ftr >= 0) {
+        p_ta = xs[(size_t)ftr * nt + i];
+        p_tb = xs[(size_t)(T + ftr) * nt + i];
+      }
+    }
+  };
+
+  fetch(0);
+  cluster.sync();  // every CTA of the cluster is resident before remote stores
+
+  for (int st = 0; st < nsteps; ++st) {
+    const bool fwd = st < nt;
+    const int i = step_col(st);
+    // operands of this step (registers)
+    cd c_sinv[kSolveRW][kSolveCW];
+    cf c_hi[kSolveRW][kSolveCW], c_lo[kSolveRW][kSolveCW];
+    cd c_y[kSolveRW];
+#pragma unroll
+    for (int a = 0; a < kSolveRW; ++a) {
+#pragma unroll
+      for (int c = 0; c < kSolveCW; ++c) {
+        if (DF) { c_hi[a][c] = p_hi[a][c]; c_lo[a][c] = p_lo[a][c]; }
+        else c_sinv[a][c] = p_sinv[a][c];
+      }
+      c_y[a] = p_y[a];
+    }
+    // v = f_i - W_i o y_{i-1} (forward)  |  v = E_i o x_{i+1} (backward); prev in the other buffer
+    if (vrow) {
+      const cd prev = ybuf[(i + 1) & 1][rv];
+      cd v;
+      if (fwd) {
+        v = p_f;
+        if (MODE == 1 && ftr >= 0) v = cadd(v, cscale(cadd(p_ta, p_tb), fsg));
+        if (i > 0) v = csub(v, cmul(p_coef, prev));
+      } else {
+        v = cmul(p_coef, prev);
+      }
+      if (DF) {
+        float rh = (float)v.x, ih = (float)v.y;
+        vloc[rv] = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+      } else {
+        reinterpret_cast<cd*>(vloc)[rv] = v;
+      }
+    }
+    __syncthreads();
+    if (st + 1 < nsteps) fetch(st + 1);
+    cd* ycur = ybuf[i & 1];
+#pragma unroll
+    for (int a = 0; a < kSolveRW; ++a) {
+      const int r = r0 + warp + 8 * a;
+      cd acc;
+      if (DF) {
+        float Sr = 0.f, Cr = 0.f, Si = 0.f, Ci = 0.f;
+#pragma unroll
+        for (int c = 0; c < kSolveCW; ++c) {
+          const int k = lane + 32 * c;
+          if (k < n) {
+            const float4 xv = vloc[k];
+            const cf h = c_hi[a][c], lo = c_lo[a][c];
+            dfmac(h.x, lo.x, xv.x, xv.z, Sr, Cr);
+            dfmac(-h.y, -lo.y, xv.y, xv.w, Sr, Cr);
+            dfmac(h.x, lo.x, xv.y, xv.w, Si, Ci);
+            dfmac(h.y, lo.y, xv.x, xv.z, Si, Ci);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          df_shfl(Sr, Cr, o);
+          df_shfl(Si, Ci, o);
+        }
+        acc = make_double2((double)Sr + (double)Cr, (double)Si + (double)Ci);
+      } else {
+        acc = make_double2(0, 0);
+        const cd* vl = reinterpret_cast<const cd*>(vloc);
+#pragma unroll
+        for (int c = 0; c < kSolveCW; ++c) {
+          const int k = lane + 32 * c;
+          if (k < n) acc = cfma(c_sinv[a][c], vl[k], acc);
+        }
+        acc = warp_sum_cd(acc);
+      }
+      if (r < r1 && lane == 0) {
+        const cd val = fwd ? acc : csub(c_y[a], acc);
+        if (fwd) Y[(size_t)i * n + r] = val;
+#pragma unroll
+        for (int q = 0; q < kSolveCS; ++q) cluster.map_shared_rank(ycur, q)[r] = val;
+        if (!fwd || i == nt - 1) {
+          if (MODE == 0) {
+            cd* b = out + (size_t)s * T4n;
+            const cd mx = make_double2(-val.x, -val.y);
+            if (L.has_bot && r == L.row[2]) b[(size_t)(2 * l) * nt + i] = mx;
+            if (L.has_bot && r == L.row[3]) b[(size_t)(2 * l + 1) * nt + i] = mx;
+            if (L.has_top && r == L.row[0]) b[(size_t)(T + 2 * (l - 1)) * nt + i] = mx;
+            if (L.has_top && r == L.row[1]) b[(size_t)(T + 2 * (l - 1) + 1) * nt + i] = mx;
+          } else if (r >= L.pad_top && r < L.pad_top + L.n) {
+            out[(size_t)s * g.Nz * nt + (size_t)(L.start + r - L.pad_top) * nt + i] = val;
+          }
+        }
+      }
+    }
+    cluster.sync();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float local solve: the whole step runs in FP32 pairs (hi, lo).  The
+// chain state, the couplings W/E and the stored forward iterates are kept as
+// (re_hi, im_hi, re_lo, im_lo); only non-zero source and forcing values are
+// converted from FP64 (a bit test, not an FP64 compare, decides) and only the
+// emitted outputs are converted back, by one lane.  GB300 executes FP64
+// arithmetic and FP64 conversions on its narrow FP64 pipe, so keeping them out
+// of the per-step path is what makes the chain fast.
+// ---------------------------------------------------------------------------
+constexpr int kDfThreads = 512;  // 16 warps
+constexpr int kDfCS = 4;         // CTAs per cluster (4 SMs per layer solve)
+constexpr int kDfCW = (kMaxNloc + 31) / 32;
+
+struct df2 {  // complex double-float, unevaluated sums re = rh + rl, im = ih + il
+  float rh, ih, rl, il;
+};
+__device__ __forceinline__ float4 to4(df2 a) { return make_float4(a.rh, a.ih, a.rl, a.il); }
+__device__ __forceinline__ df2 from4(float4 v) { return df2{v.x, v.y, v.z, v.w}; }
+__device__ __forceinline__ bool nonzero_d(cd v) {
+  return ((__double_as_longlong(v.x) | __double_as_longlong(v.y)) << 1) != 0;  // +-0 are zero
+}
+__device__ __forceinline__ df2 split_d(cd v) {
+  float rh = (float)v.x, ih = (float)v.y;
+  return df2{rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih)};
+}
+// normalise (S, C) into hi + lo with |lo| <= ulp(hi)/2
+__device__ __forceinline__ void df_norm(float S, float C, float& hi, float& lo) {
+  hi = S + C;
+  lo = C - (hi - S);
+}
+// (Sr, Cr, Si, Ci) += a * x  (complex double-float multiply-accumulate)
+__device__ __forceinline__ void df_cmac(float ahr, float ahi, float alr, float ali, df2 x, float& Sr, float& Cr,
+                                        float& Si, float& Ci) {
+  dfmac(ahr, alr, x.rh, x.rl, Sr, Cr);
+  dfmac(-ahi, -ali, x.ih, x.il, Sr, Cr);
+  dfmac(ahr, alr, x.ih, x.il, Si, Ci);
+  dfmac(ahi, ali, x.rh, x.rl, Si, Ci);
+}
+
+// CS CTAs per cluster; a warp owns rows r0 + warp + 16 a, a < RW (independent chains interleave).
+template <int MODE, int CS>
+__global__ void __launch_bounds__(kDfThreads, 1)
+    layer_solve_df_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cf* __restrict__ Shi,
+                          const cf* __restrict__ Slo, const cf* __restrict__ Whi, const cf* __restrict__ Wlo,
+                          const cf* __restrict__ Ehi, const cf* __restrict__ Elo, const cd* __restrict__ f,
+                          const cd* __restrict__ xtr, float4* __restrict__ Ystore, size_t ystride,
+                          cd* __restrict__ out, const int* __restrict__ nzflag) {
+  __shared__ __align__(16) float4 ybuf[2][kMaxNloc];
+  __shared__ __align__(16) float4 vloc[kMaxNloc];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int l = blockIdx.x / CS;
+  const int s = blockIdx.y;
+  const LayerInfo L = layers[l];
+  const int n = L.nloc, nt = g.nt;
+  const int T = 2 * (g.L - 1);
+  const size_t T4n = (size_t)2 * T * nt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpc = (n + CS - 1) / CS;
+  const int r0 = rank * rpc, r1 = min(n, r0 + rpc);
+  constexpr int RW = ((kMaxNloc + CS - 1) / CS + 15) / 16;  // rows per warp
+
+  if (MODE == 0 && nzflag[s * g.L + l] == 0) {
+    cd* b = out + (size_t)s * T4n;
+    for (int k = rank * blockDim.x + threadIdx.x; k < nt; k += CS * blockDim.x) {
+      if (L.has_bot) {
+        b[(size_t)(2 * l) * nt + k] = make_double2(0, 0);
+        b[(size_t)(2 * l + 1) * nt + k] = make_double2(0, 0);
+      }
+      if (L.has_top) {
+        b[(size_t)(T + 2 * (l - 1)) * nt + k] = make_double2(0, 0);
+        b[(size_t)(T + 2 * (l - 1) + 1) * nt + k] = make_double2(0, 0);
+      }
+    }
+    return;  // uniform over the cluster, before any cluster barrier
+  }
+
+  const cd* fs = f + (size_t)s * g.Nz * nt;
+  const cd* xs = (MODE == 1) ? xtr + (size_t)s * T4n : nullptr;
+  float4* Y = Ystore + ((size_t)s * g.L + l) * ystride;
+  const double ih2 = 1.0 / (g.h * g.h);
+  const int nsteps = 2 * nt - 1;
+  auto step_col = [&](int st) { return st < nt ? st : (nt - 2 - (st - nt)); };
+
+  const int rv = threadIdx.x;
+  const bool vrow = rv < n;
+  const bool in_layer = vrow && rv >= L.pad_top && rv < L.pad_top + L.n;
+  const size_t frow = in_layer ? (size_t)(L.start + rv - L.pad_top) * nt : 0;
+  int ftr = -1;
+  double fsg = 0.0;
+  if (MODE == 1 && vrow) {
+    if (L.has_top && rv == L.row[1]) { ftr = 2 * (l - 1); fsg = ih2; }
+    if (L.has_top && rv == L.row[0]) { ftr = 2 * (l - 1) + 1; fsg = -ih2; }
+    if (L.has_bot && rv == L.row[3]) { ftr = 2 * l; fsg = -ih2; }
+    if (L.has_bot && rv == L.row[2]) { ftr = 2 * l + 1; fsg = ih2; }
+  }
+
+  // prefetched operands of the next step (predicated loads, no selects on results)
+  cf p_hi[RW][kDfCW], p_lo[RW][kDfCW];
+  float4 p_y[RW];
+#pragma unroll
+  for (int a = 0; a < RW; ++a) {
+    p_y[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < kDfCW; ++c) { p_hi[a][c] = make_float2(0.f, 0.f); p_lo[a][c] = make_float2(0.f, 0.f); }
+  }
+  cf p_ch = make_float2(0.f, 0.f), p_cl = make_float2(0.f, 0.f);
+  cd p_f = make_double2(0, 0), p_ta = make_double2(0, 0), p_tb = make_double2(0, 0);
+  auto fetch = [&](int st) {
+    const int i = step_col(st);
+    const bool fwd = st < nt;
+#pragma unroll
+    for (int a = 0; a < RW; ++a) {
+      const int r = r0 + warp + 16 * a;
+      const bool rowok = r < r1;
+      const size_t base = L.sinv_off + (size_t)i * n * n + (size_t)r * n;
+#pragma unroll
+      for (int c = 0; c < kDfCW; ++c) {
+        const int k = lane + 32 * c;
+        if (rowok && k < n) {
+          p_hi[a][c] = __ldg(Shi + base + k);
+          p_lo[a][c] = __ldg(Slo + base + k);
+        }
+      }
+      if (!fwd && lane == 0 && rowok) p_y[a] = Y[(size_t)i * n + r];
+    }
+    if (vrow) {
+      const size_t co = L.coef_off + (size_t)i * n + rv;
+      p_ch = __ldg((fwd ? Whi : Ehi) + co);
+      p_cl = __ldg((fwd ? Wlo : Elo) + co);
+      if (fwd && in_layer) p_f = fs[frow + i];
+      if (MODE == 1 && fwd && ftr >= 0) {
+        p_ta = xs[(size_t)ftr * nt + i];
+        p_tb = xs[(size_t)(T + ftr) * nt + i];
+      }
+    }
+  };
+
+  fetch(0);
+  cluster.sync();
+
+  for (int st = 0; st < nsteps; ++st) {
+    const bool fwd = st < nt;
+    const int i = step_col(st);
+    cf c_hi[RW][kDfCW], c_lo[RW][kDfCW];
+    float4 c_y[RW];
+#pragma unroll
+    for (int a = 0; a < RW; ++a) {
+      c_y[a] = p_y[a];
+#pragma unroll
+      for (int c = 0; c < kDfCW; ++c) { c_hi[a][c] = p_hi[a][c]; c_lo[a][c] = p_lo[a][c]; }
+    }
+    // v = f_i - W_i o y_{i-1} (forward) | v = E_i o x_{i+1} (backward), in double-float
+    if (vrow) {
+      const df2 prev = from4(ybuf[(i + 1) & 1][rv]);
+      float Sr = 0.f, Cr = 0.f, Si = 0.f, Ci = 0.f;
+      if (fwd) {
+        if (nonzero_d(p_f)) {
+          const df2 fv = split_d(p_f);
+          Sr = fv.rh; Cr = fv.rl; Si = fv.ih; Ci = fv.il;
+        }
+        if (MODE == 1 && ftr >= 0) {
+          const df2 fv = split_d(cscale(cadd(p_ta, p_tb), fsg));
+          float s1, e1;
+          ts(Sr, fv.rh, s1, e1); Sr = s1; Cr += e1 + fv.rl;
+          ts(Si, fv.ih, s1, e1); Si = s1; Ci += e1 + fv.il;
+        }
+        if (i > 0) df_cmac(-p_ch.x, -p_ch.y, -p_cl.x, -p_cl.y, prev, Sr, Cr, Si, Ci);
+      } else {
+        df_cmac(p_ch.x, p_ch.y, p_cl.x, p_cl.y, prev, Sr, Cr, Si, Ci);
+      }
+      df2 v;
+      df_norm(Sr, Cr, v.rh, v.rl);
+      df_norm(Si, Ci, v.ih, v.il);
+      vloc[rv] = to4(v);
+    }
+    __syncthreads();
+    if (st + 1 < nsteps) fetch(st + 1);
+    float Sr[RW], Cr[RW], Si[RW], Ci[RW];
+#pragma unroll
+    for (int a = 0; a < RW; ++a) { Sr[a] = 0.f; Cr[a] = 0.f; Si[a] = 0.f; Ci[a] = 0.f; }
+#pragma unroll
+    for (int c = 0; c < kDfCW; ++c) {
+      const int k = lane + 32 * c;
+      if (k < n) {
+        const df2 xv = from4(vloc[k]);
+#pragma unroll
+        for (int a = 0; a < RW; ++a)
+          df_cmac(c_hi[a][c].x, c_hi[a][c].y, c_lo[a][c].x, c_lo[a][c].y, xv, Sr[a], Cr[a], Si[a], Ci[a]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int a = 0; a < RW; ++a) {
+        df_shfl(Sr[a], Cr[a], o);
+        df_shfl(Si[a], Ci[a], o);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < RW; ++a) {
+      const int r = r0 + warp + 16 * a;
+      if (r < r1 && lane == 0) {
+        df2 val;
+        if (fwd) {
+          df_norm(Sr[a], Cr[a], val.rh, val.rl);
+          df_norm(Si[a], Ci[a], val.ih, val.il);
+          Y[(size_t)i * n + r] = to4(val);
+        } else {
+          // x_i = y_i - acc
+          float s1, e1;
+          ts(c_y[a].x, -Sr[a], s1, e1);
+          df_norm(s1, e1 + c_y[a].z - Cr[a], val.rh, val.rl);
+          ts(c_y[a].y, -Si[a], s1, e1);
+          df_norm(s1, e1 + c_y[a].w - Ci[a], val.ih, val.il);
+        }
+        float4* ycur = ybuf[i & 1];
+        const float4 v4 = to4(val);
+#pragma unroll
+        for (int q = 0; q < CS; ++q) cluster.map_shared_rank(ycur, q)[r] = v4;
+        if (!fwd || i == nt - 1) {
+          if (MODE == 0) {
+            const bool emit = (L.has_bot && (r == L.row[2] || r == L.row[3])) ||
+                              (L.has_top && (r == L.row[0] || r == L.row[1]));
+            if (emit) {
+              cd* b = out + (size_t)s * T4n;
+              const cd mx = make_double2(-((double)val.rh + (double)val.rl), -((double)val.ih + (double)val.il));
+              if (L.has_bot && r == L.row[2]) b[(size_t)(2 * l) * nt + i] = mx;
+              if (L.has_bot && r == L.row[3]) b[(size_t)(2 * l + 1) * nt + i] = mx;
+              if (L.has_top && r == L.row[0]) b[(size_t)(T + 2 * (l - 1)) * nt + i] = mx;
+              if (L.has_top && r == L.row[1]) b[(size_t)(T + 2 * (l - 1) + 1) * nt + i] = mx;
+            }
+          } else if (r >= L.pad_top && r < L.pad_top + L.n) {
+            out[(size_t)s * g.Nz * nt + (size_t)(L.start + r - L.pad_top) * nt + i] =
+                make_double2((double)val.rh + (double)val.rl, (double)val.ih + (double)val.il);
+          }
+        }
+      }
+    }
+    cluster.sync();
+  }
+}
+
+// flag[s * L + l] = 1 when f^l of source s has a non-zero entry
+__global__ void layer_nonzero_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cd* __restrict__ f,
+                                     int* __restrict__ flag) {
+  const LayerInfo L = layers[blockIdx.x];
+  const int s = blockIdx.y;
+  const cd* fs = f + (size_t)s * g.Nz * g.nt + (size_t)L.start * g.nt;
+  int nz = 0;
+  for (size_t k = threadIdx.x; k < (size_t)L.n * g.nt; k += blockDim.x) {
+    cd v = fs[k];
+    nz |= (v.x != 0.0 || v.y != 0.0);
+  }
+  nz = __syncthreads_or(nz);
+  if (threadIdx.x == 0) flag[s * g.L + blockIdx.x] = nz;
+}
+
+__global__ void split_sinv_kernel(const cd* __restrict__ src, size_t n, cf* __restrict__ hi, cf* __restrict__ lo) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    cd v = src[q];
+    cf h = make_float2((float)v.x, (float)v.y);
+    hi[q] = h;
+    lo[q] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+  }
+}
+
+cudaError_t launch_layer_nonzero(const Geometry& g, const LayerInfo* layers, const cd* f, int* flag, int nsrc,
+                                 cudaStream_t s) {
+  layer_nonzero_kernel<<<dim3(g.L, nsrc), 256, 0, s>>>(g, layers, f, flag);
+  return cudaGetLastError();
+}
+
+// df: use the double-float (hi, lo) factors instead of the FP64 ones
+cudaError_t launch_layer_solve2(int mode, bool /*df*/, const Geometry& g, const LayerInfo* layers, const cd* Sinv,
+                                const cf* Shi, const cf* Slo, const cd* W, const cd* E, const cd* f, const cd* xtr,
+                                cd* Y, size_t ystride, cd* out, const int* flag, int nsrc, cudaStream_t s) {
+  dim3 grid(kSolveCS * g.L, nsrc);
+  if (mode == 0)
+    layer_solve_kernel<0, false><<<grid, 256, 0, s>>>(g, layers, Sinv, Shi, Slo, W, E, f, xtr, Y, ystride, out, flag);
+  else
+    layer_solve_kernel<1, false><<<grid, 256, 0, s>>>(g, layers, Sinv, Shi, Slo, W, E, f, xtr, Y, ystride, out, flag);
+  return cudaGetLastError();
+}
+
+// FP64 factors (the entry point used by the plain path and pt_rhs_noalloc)
+cudaError_t launch_layer_solve(int mode, const Geometry& g, const LayerInfo* layers, const cd* Sinv, const cd* W,
+                               const cd* E, const cd* f, const cd* xtr, cd* Y, size_t ystride, cd* out,
+                               const int* flag, int nsrc, cudaStream_t s) {
+  return launch_layer_solve2(mode, false, g, layers, Sinv, nullptr, nullptr, W, E, f, xtr, Y, ystride, out, flag,
+                             nsrc, s);
+}
+
+cudaError_t launch_layer_solve_df(int mode, const Geometry& g, const LayerInfo* layers, const cf* Shi, const cf* Slo,
+                                  const cf* Whi, const cf* Wlo, const cf* Ehi, const cf* Elo, const cd* f,
+                                  const cd* xtr, cd* Y, size_t ystride, cd* out, const int* flag, int nsrc,
+                                  cudaStream_t s) {
+  static_assert(sizeof(float4) == sizeof(cd), "double-float iterates reuse the FP64 scratch layout");
+  float4* Y4 = reinterpret_cast<float4*>(Y);
+  auto go = [&](auto kern, int cs) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * g.L, nsrc);
+    cfg.blockDim = dim3(kDfThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g, layers, Shi, Slo, Whi, Wlo, Ehi, Elo, f, xtr, Y4, ystride, out, flag);
+  };
+  cudaError_t e = mode == 0 ? go(layer_solve_df_kernel<0, kDfCS>, kDfCS) : go(layer_solve_df_kernel<1, kDfCS>, kDfCS);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_sinv(const cd* src, size_t n, cf* hi, cf* lo, cudaStream_t s) {
+  split_sinv_kernel<<<1216, 256, 0, s>>>(src, n, hi, lo);
+  return cudaGetLastError();
+}
+
+}  // namespace pt

@@ -116,6 +116,9 @@ def test_mixed_fp32_preconditioner_meets_mixed_tolerance(small):
     mask = D.physical_mask(prob, wl.nx, wl.nz)
     assert rel[0] <= 1e-9
     assert _rel(u.cpu().numpy()[0][mask], u_ref[mask]) < 1e-5
+    # the matvec and local solves of the mixed form are double-float (~1e-13), so the
+    # field is as close to the oracle as the GMRES tolerance allows
+    assert _rel(u.cpu().numpy()[0], u_ref) < 1e-7
 
 
 def test_batched_sources_equal_single_solves():
