@@ -216,6 +216,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=20, help="oracle back-substitutions in cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-plr", action="store_true", help="skip the partitioned low-rank variants")
+    ap.add_argument("--plr-eps", type=float, default=1e-9)
+    ap.add_argument("--plr-rmax", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -242,10 +245,10 @@ def main():
     f_dev = torch.from_numpy(f_host).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def make(prec):
+    def make(prec, plr=False):
         t0 = time.perf_counter()
         s = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, om, c_dev, pml_C=pmlC, precision=prec, max_sources=S,
-                       max_krylov=40)
+                       max_krylov=40, plr=plr, plr_eps=args.plr_eps, plr_rmax=args.plr_rmax)
         torch.cuda.synchronize(dev)
         return s, time.perf_counter() - t0
 
@@ -286,6 +289,22 @@ def main():
         plain = {"value": total_solves / (max_over_ranks(pg, ms64) / 1e3),
                  "ms_per_step": ms64, "gmres_iterations": its64, "true_relres": rel64, "offline_s": t_off64}
         extra["volume_rel_diff_vs_fp64"] = diff
+
+    # partitioned low-rank blocks (Algorithm 5, eps and r_max of the workload), FP64 and mixed
+    plr_results = {}
+    if not args.no_plr:
+        for name, prec in (("plr_fp64", PT_FP64), ("plr_mixed", PT_MIXED_FP32)):
+            ps, t_offp = make(prec, plr=True)
+            msp, itsp, relp, up, _ = time_solves(ps, max(2, args.steps // 2), 3)
+            stored, leaves = ps.plr_stats()
+            dense_entries = (16 * (wl.L - 2) + 8) * wl.nt * wl.nt
+            plr_results[name] = {
+                "value": total_solves / (max_over_ranks(pg, msp) / 1e3), "ms_per_step": msp,
+                "gmres_iterations": itsp, "true_relres": relp, "offline_s": t_offp, "leaves": leaves,
+                "compression": dense_entries / stored,
+                "volume_rel_diff_vs_chosen": float(torch.linalg.vector_norm(up - u) / torch.linalg.vector_norm(u))}
+            del ps
+            torch.cuda.empty_cache()
 
     # ---- roofline of the block-apply kernel (the interface-system matvec, one launch) ----
     pk, pk_kind = peaks()
@@ -346,6 +365,7 @@ def main():
         }
         if plain is not None:
             line["plain_fp64"] = plain
+        line.update(plr_results)
         line.update(extra)
         print(json.dumps(line), flush=True)
 

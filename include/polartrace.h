@@ -79,6 +79,12 @@ typedef struct {
   int32_t gs_iters;   /* n_it of Algorithm 4 (the paper uses 2)                      */
   int32_t max_sources;/* largest nsrc a pt_solve call may use                       */
   int32_t max_krylov; /* largest GMRES iteration count a pt_solve call may use      */
+  int32_t plr;        /* 1: compress the interface blocks to partitioned low rank
+                         (Section 5.1, Algorithm 5) and apply them in the GMRES matvec
+                         and the preconditioner; 0: dense blocks                     */
+  double plr_eps;     /* relative threshold: a node is a leaf when sigma_{r_max+1}
+                         < plr_eps * sigma_1 of its whole block                      */
+  int32_t plr_rmax;   /* r_max, 1 .. 31                                              */
 } pt_params;
 
 /* Layer partition used by the library (Section 2.2): the first (N_z mod L)
@@ -181,6 +187,23 @@ pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y, void* 
  *   that overlap on the GPU (other streams, other threads) race on the array.
  *   The call returns after its work on the context's stream has finished. */
 pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y);
+
+/* One operator of the permuted polarized jump system in the representation
+ * the solver works with.  which: 0 = P M (Definition 9), 1 = R, 2 = D^{-1}
+ * (the sweeps of Section 4.1).  working = 0: dense FP64 blocks (the exact
+ * operator, as pt_apply_matvec / pt_apply_R / pt_apply_D_inverse);
+ * working = 1: what pt_solve uses for it - the partitioned low-rank blocks
+ * when the context compresses (plr = 1), FP32 blocks for R and D^{-1} in the
+ * mixed precision, double-float for P M in the mixed precision.  x and y are
+ * device trace vectors (nsrc of them), scratch >= solve_bytes. */
+pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32_t nsrc, const pt_c128* x, pt_c128* y,
+                   void* scratch, size_t scratch_bytes);
+
+/* Size of the partitioned low-rank representation built by pt_create with
+ * plr = 1 (Algorithm 5): complex entries stored (dense leaves count m n,
+ * low-rank leaves r (m + n)) and number of leaves, both host outputs (NULL
+ * allowed).  Zero when the context keeps dense blocks. */
+pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leaves);
 
 /* Copy the interface Green's matrix G^l(z_j, z_k) / h (the block that the
  * incomplete Green's integrals of Definition 2 multiply) to dst (device,

@@ -26,8 +26,10 @@ def default_pml_strength(c_max: float) -> float:
     return 1.5 * c_max * math.log(1.0e6)
 
 
-def _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov) -> Params:
-    return Params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov)
+def _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr=0, plr_eps=1e-9,
+            plr_rmax=24) -> Params:
+    return Params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr, plr_eps,
+                  plr_rmax)
 
 
 def layer_partition(nx, nz, npml, L) -> list:
@@ -47,7 +49,8 @@ class PolarTrace:
 
     def __init__(self, nx: int, nz: int, npml: int, L: int, h: float, omega: float, c_ext: torch.Tensor,
                  pml_C: float | None = None, precision: int = PT_FP64, gs_iters: int = 2, max_sources: int = 1,
-                 max_krylov: int = 40, stream: torch.cuda.Stream | None = None):
+                 max_krylov: int = 40, stream: torch.cuda.Stream | None = None, plr: bool = False,
+                 plr_eps: float = 1e-9, plr_rmax: int = 24):
         if not (c_ext.is_cuda and c_ext.dtype == torch.float64 and c_ext.is_contiguous()):
             raise ValueError("c_ext must be a contiguous float64 CUDA tensor of shape (N_z, n_t)")
         self.nx, self.nz, self.npml, self.L = nx, nz, npml, L
@@ -56,7 +59,8 @@ class PolarTrace:
             raise ValueError(f"c_ext must have shape {(self.Nz, self.nt)}")
         if pml_C is None:
             pml_C = default_pml_strength(float(c_ext.max()))
-        self.params = _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov)
+        self.params = _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov,
+                              int(plr), plr_eps, plr_rmax)
         self.max_sources, self.max_krylov = max_sources, max_krylov
         self.device = c_ext.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -140,6 +144,20 @@ class PolarTrace:
     # ---- building blocks (testing) -----------------------------------------
     def _vec(self, S):
         return torch.empty((S, self.T4, self.nt), dtype=torch.complex128, device=self.device)
+
+    def apply(self, which: str, x: torch.Tensor, working: bool = True) -> torch.Tensor:
+        """One operator ('matvec', 'R', 'Dinv') in the solver's working representation (or dense FP64)."""
+        y = torch.empty_like(x)
+        w = {"matvec": 0, "R": 1, "Dinv": 2}[which]
+        check(lib().pt_apply(self._ctx, w, int(working), x.shape[0], _ptr(x), _ptr(y), _ptr(self._scratch),
+                             self._scratch.numel()), "pt_apply")
+        return y
+
+    def plr_stats(self):
+        n = C.c_int64()
+        m = C.c_int32()
+        check(lib().pt_plr_stats(self._ctx, C.byref(n), C.byref(m)), "pt_plr_stats")
+        return n.value, m.value
 
     def matvec(self, x: torch.Tensor) -> torch.Tensor:
         y = torch.empty_like(x)

@@ -21,7 +21,7 @@ STATUS = ["PT_OK", "PT_ERR_ARG", "PT_ERR_WORKSPACE", "PT_ERR_CUDA", "PT_ERR_SING
 EXPORTS = [
     "pt_layer_partition", "pt_workspace_size", "pt_create", "pt_solve", "pt_solve_host", "pt_apply_matvec",
     "pt_apply_precond", "pt_apply_D_inverse", "pt_apply_R", "pt_rhs", "pt_get_block", "pt_last_solve_stats",
-    "pt_destroy", "pt_status_string", "pt_last_error", "pt_rhs_noalloc",
+    "pt_destroy", "pt_status_string", "pt_last_error", "pt_rhs_noalloc", "pt_apply", "pt_plr_stats",
 ]
 
 
@@ -30,6 +30,7 @@ class Params(C.Structure):
         ("nx", C.c_int32), ("nz", C.c_int32), ("npml", C.c_int32), ("L", C.c_int32),
         ("h", C.c_double), ("omega", C.c_double), ("pml_C", C.c_double),
         ("precision", C.c_int32), ("gs_iters", C.c_int32), ("max_sources", C.c_int32), ("max_krylov", C.c_int32),
+        ("plr", C.c_int32), ("plr_eps", C.c_double), ("plr_rmax", C.c_int32),
     ]
 
 
@@ -63,6 +64,8 @@ def lib() -> C.CDLL:
     L.pt_apply_precond.argtypes = [vp, i32, vp, vp, vp, sz]
     L.pt_rhs.argtypes = [vp, i32, vp, vp, vp, sz]
     L.pt_rhs_noalloc.argtypes = [vp, i32, vp, vp]
+    L.pt_apply.argtypes = [vp, i32, i32, i32, vp, vp, vp, sz]
+    L.pt_plr_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
     L.pt_get_block.argtypes = [vp, i32, i32, i32, vp]
     L.pt_last_solve_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
     L.pt_destroy.argtypes = [vp]

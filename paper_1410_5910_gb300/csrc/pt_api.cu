@@ -38,6 +38,14 @@ cudaError_t launch_layer_solve_df(int, const Geometry&, const LayerInfo*, const 
                                   const cf*, const cf*, const cd*, const cd*, cd*, size_t, cd*, const int*, int,
                                   cudaStream_t);
 int dot_chunks(size_t N);
+size_t plr_scratch_per_cta(int nt);
+int plr_max_k();
+cudaError_t launch_plr_compress(int, const cd*, const int*, int, int, double, int, cd*, int, PlrLeaf*, int, int*, cd*,
+                                int*, cudaStream_t);
+cudaError_t launch_plr_apply(bool, int, int, int, const ApplyRow*, int, const void*, const void*, const PlrLeaf*,
+                             const PlrTask*, int, const int*, const int*, const int*, const int*, cd*, int, const cd*,
+                             const cd*, cd*, int, double, double, cudaStream_t);
+cudaError_t launch_pool_to_fp32(const cd*, cf*, size_t, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
 cudaError_t launch_norm_scale(const cd*, size_t, int, double*, cd*, int, int, int, int, cd*, size_t,
@@ -69,6 +77,8 @@ constexpr size_t kAlign = 256;
 constexpr int kExtractSlots = 152;
 constexpr int kApplyRowsSweep = 8;   // rows per CTA for the sweep steps
 constexpr int kApplyRowsWide = 16;   // rows per CTA for R and the matvec
+constexpr int kPlrCap = 512;         // leaves per compressed block
+constexpr int kPlrSlots = 152;       // CTAs of the compression kernel
 
 struct Carver {
   char* base;
@@ -92,6 +102,11 @@ struct Plan {
   std::vector<LayerInfo> layers;
   std::vector<ExtractTask> tasks;
   size_t sinv_elems = 0, coef_elems = 0;
+  // partitioned low-rank blocks
+  bool plr = false;
+  int rmax = 0, oversample = 0, ntiles = 0;
+  std::vector<int> plr_blocks;  // absolute block slots (layer * 16 + jk) that exist
+  size_t plr_task_cap = 0;      // projection tasks of one operator table, upper bound
 };
 
 pt_status make_plan(const pt_params* p, Plan& P) {
@@ -142,6 +157,24 @@ pt_status make_plan(const pt_params* p, Plan& P) {
   }
   if (P.nloc_max > kMaxNloc)
     return fail(PT_ERR_ARG, "a local problem has more than 118 rows (layer rows + 2 n_pml); use more layers");
+  if (p->plr) {
+    if (p->plr_rmax < 1 || p->plr_rmax > 31 || !(p->plr_eps > 0) || !std::isfinite(p->plr_eps))
+      return fail(PT_ERR_ARG, "plr needs 1 <= plr_rmax <= 31 and plr_eps > 0");
+    P.plr = true;
+    P.rmax = p->plr_rmax;
+    P.oversample = std::min(8, plr_max_k() - 1 - P.rmax);
+    P.ntiles = (P.nt + 31) / 32;
+    for (int l = 0; l < P.L; ++l) {
+      const LayerInfo& I = P.layers[l];
+      for (int jj = 0; jj < 4; ++jj)
+        for (int kk = 0; kk < 4; ++kk) {
+          const bool jo = (jj < 2) ? I.has_top : I.has_bot;
+          const bool ko = (kk < 2) ? I.has_top : I.has_bot;
+          if (jo && ko) P.plr_blocks.push_back(l * 16 + jj * 4 + kk);
+        }
+    }
+    P.plr_task_cap = (size_t)P.T4 * 4 * kPlrCap;
+  }
   // extraction tasks: 32 right-hand sides each
   for (int l = 0; l < P.L; ++l) {
     ExtractTask t{};
@@ -174,6 +207,21 @@ struct Persist {
   ApplyRow* tab_R;
   ApplyRow* tab_sweep;
   ExtractTask* tasks;
+  // PLR
+  PlrLeaf* leaves;      // [nblk][kPlrCap]
+  int* nleaves;         // [nblk]
+  int* plr_ids;         // [nblk] absolute block slots
+  cd* pool;             // [nblk][nt * nt] factors
+  cf* pool32;           // mixed form: FP32 copy
+  int* lr_ord;          // [nblk * cap] ordinal among the low-rank leaves of the block
+  int* tile_ptr;        // [L * 16 * ntiles + 1]
+  int* tile_leaf;       // CSR entries
+  PlrTask* task_mv;     // matvec table
+  int* tbase_mv;
+  PlrTask* task_R;      // coupling table
+  int* tbase_R;
+  PlrTask* task_sw;     // sweep steps, (L-1) x 4 rows
+  int* tbase_sw;
 };
 
 Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* bytes) {
@@ -201,6 +249,23 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
   q.tab_R = c.take<ApplyRow>(P.T4);
   q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
   q.tasks = c.take<ExtractTask>(P.tasks.size());
+  if (P.plr) {
+    const size_t nb = P.plr_blocks.size();
+    q.leaves = c.take<PlrLeaf>(nb * kPlrCap);
+    q.nleaves = c.take<int>(nb);
+    q.plr_ids = c.take<int>(nb);
+    q.pool = c.take<cd>(nb * P.nt * P.nt);
+    if (p->precision == PT_MIXED_FP32) q.pool32 = c.take<cf>(nb * P.nt * P.nt);
+    q.lr_ord = c.take<int>(nb * kPlrCap);
+    q.tile_ptr = c.take<int>((size_t)P.L * 16 * P.ntiles + 1);
+    q.tile_leaf = c.take<int>(nb * kPlrCap * (size_t)P.ntiles);
+    q.task_mv = c.take<PlrTask>(P.plr_task_cap);
+    q.tbase_mv = c.take<int>((size_t)P.T4 * 4);
+    q.task_R = c.take<PlrTask>(P.plr_task_cap);
+    q.tbase_R = c.take<int>((size_t)P.T4 * 4);
+    q.task_sw = c.take<PlrTask>(P.plr_task_cap);
+    q.tbase_sw = c.take<int>((size_t)(P.L - 1) * 16);
+  }
   if (bytes) *bytes = c.off;
   return q;
 }
@@ -214,6 +279,15 @@ size_t setup_bytes_of(const Plan& P) {
   return c.off;
 }
 
+// The PLR compressor reuses the setup workspace after the extraction.
+size_t plr_setup_bytes(const Plan& P) {
+  if (!P.plr) return 0;
+  Carver c(nullptr);
+  const int nslots = std::min<int>((int)P.plr_blocks.size(), kPlrSlots);
+  c.take<cd>(plr_scratch_per_cta(P.nt) * nslots);
+  return c.off;
+}
+
 struct SolveBufs {
   cd* Y;
   int* nzflag;
@@ -221,6 +295,7 @@ struct SolveBufs {
   double *cs, *resid, *nrm;
   int* kk;
   cd *fdev, *udev;  // pt_solve_host staging
+  cd* tbuf;         // PLR projections
 };
 
 SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base, size_t* bytes) {
@@ -246,6 +321,7 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
   b.resid = c.take<double>(S);
   b.nrm = c.take<double>(S);
   b.kk = c.take<int>(S);
+  b.tbuf = P.plr ? c.take<cd>((size_t)S * P.plr_task_cap * P.rmax) : nullptr;
   if (host_staging) {
     b.fdev = c.take<cd>((size_t)S * P.Nz * P.nt);
     b.udev = c.take<cd>((size_t)S * P.Nz * P.nt);
@@ -368,6 +444,12 @@ struct pt_ctx {
   int64_t launches = 0;
   int last_max_it = 0;
   std::vector<double> resid_h;
+  // PLR projection task counts per operator table
+  int ntask_mv = 0, ntask_R = 0;
+  std::vector<int> sw_off, sw_cnt;
+  size_t plr_stored = 0;  // complex entries of the compressed representation
+  int plr_leaves = 0;
+  cd* tbuf = nullptr;     // projection buffer of the current call
 };
 
 static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
@@ -400,7 +482,7 @@ extern "C" pt_status pt_workspace_size(const pt_params* prm, size_t* persistent_
   carve_persist(P, prm, nullptr, &pb);
   carve_solve(P, prm->max_sources, prm->max_krylov, false, nullptr, &sb);
   if (persistent_bytes) *persistent_bytes = pb;
-  if (setup_bytes) *setup_bytes = setup_bytes_of(P);
+  if (setup_bytes) *setup_bytes = std::max(setup_bytes_of(P), plr_setup_bytes(P));
   if (solve_bytes) *solve_bytes = sb;
   return PT_OK;
 }
@@ -412,6 +494,96 @@ static pt_status read_status(pt_ctx* c) {
   if (st & kErrNumeric) return fail(PT_ERR_NUMERIC, "non-finite or non-positive value met on the device");
   if (st & kErrSingular) return fail(PT_ERR_SINGULAR, "zero pivot in a local factorization");
   if (st & kErrTimeout) return fail(PT_ERR_TIMEOUT, "a device-side wait gave up");
+  return PT_OK;
+}
+
+// Algorithm 5 on every interface block, then the host-side tables of the
+// flattened application: per-block leaf ordinals, the (block, row tile) CSR
+// of covering leaves and the projection tasks of each operator table.
+static pt_status compress_blocks(pt_ctx* c, void* setup, const std::vector<ApplyRow>& mv,
+                                 const std::vector<ApplyRow>& rr, const std::vector<ApplyRow>& sw) {
+  const Plan& P = c->P;
+  cudaStream_t s = c->stream;
+  const int nb = (int)P.plr_blocks.size();
+  const int nslots = std::min(nb, kPlrSlots);
+  PT_CUDA(cudaMemcpyAsync(c->d.plr_ids, P.plr_blocks.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+  PT_CUDA(launch_plr_compress(P.nt, c->d.blocks, c->d.plr_ids, nb, P.rmax, c->prm.plr_eps, P.oversample,
+                              static_cast<cd*>(setup), nslots, c->d.leaves, kPlrCap, c->d.nleaves, c->d.pool,
+                              c->d.status, s));
+  std::vector<int> nl(nb);
+  std::vector<PlrLeaf> lv((size_t)nb * kPlrCap);
+  PT_CUDA(cudaMemcpyAsync(nl.data(), c->d.nleaves, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(cudaMemcpyAsync(lv.data(), c->d.leaves, lv.size() * sizeof(PlrLeaf), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(cudaStreamSynchronize(s));
+  pt_status st = read_status(c);
+  if (st != PT_OK) return st;
+  std::vector<int> bmap((size_t)P.L * 16, -1);
+  for (int b = 0; b < nb; ++b) bmap[P.plr_blocks[b]] = b;
+  std::vector<int> lr((size_t)nb * kPlrCap, 0);
+  std::vector<std::vector<int>> bucket((size_t)P.L * 16 * P.ntiles);
+  c->plr_stored = 0;
+  c->plr_leaves = 0;
+  for (int b = 0; b < nb; ++b) {
+    int ord = 0;
+    for (int i = 0; i < nl[b]; ++i) {
+      const PlrLeaf& f = lv[(size_t)b * kPlrCap + i];
+      const int li = b * kPlrCap + i;
+      if (f.kind == 1) lr[li] = ord++;
+      c->plr_stored += f.kind == 1 ? (size_t)f.rank * (f.m + f.n) : (size_t)f.m * f.n;
+      c->plr_leaves++;
+      for (int t = f.r0 / 32; t <= (f.r0 + f.m - 1) / 32; ++t)
+        bucket[(size_t)P.plr_blocks[b] * P.ntiles + t].push_back(li);
+    }
+  }
+  std::vector<int> tptr(bucket.size() + 1, 0), tleaf;
+  for (size_t q = 0; q < bucket.size(); ++q) {
+    tptr[q] = (int)tleaf.size();
+    tleaf.insert(tleaf.end(), bucket[q].begin(), bucket[q].end());
+  }
+  tptr[bucket.size()] = (int)tleaf.size();
+  auto build = [&](const ApplyRow* rows, int nrows, std::vector<PlrTask>& tasks, std::vector<int>& tbase) {
+    tbase.assign((size_t)nrows * 4, 0);
+    for (int r = 0; r < nrows; ++r)
+      for (int t = 0; t < rows[r].nterms; ++t) {
+        const int b = bmap[rows[r].t[t].block];
+        tbase[r * 4 + t] = (int)tasks.size();
+        for (int i = 0; i < nl[b]; ++i)
+          if (lv[(size_t)b * kPlrCap + i].kind == 1) tasks.push_back(PlrTask{r, t, b * kPlrCap + i});
+      }
+  };
+  std::vector<PlrTask> tmv, trr, tsw;
+  std::vector<int> bmv, brr, bsw;
+  build(mv.data(), (int)mv.size(), tmv, bmv);
+  build(rr.data(), (int)rr.size(), trr, brr);
+  c->sw_off.clear();
+  c->sw_cnt.clear();
+  for (int step = 0; step + 1 < P.L; ++step) {
+    std::vector<PlrTask> t1;
+    std::vector<int> b1;
+    build(sw.data() + 4 * step, 4, t1, b1);
+    c->sw_off.push_back((int)tsw.size());
+    c->sw_cnt.push_back((int)t1.size());
+    for (int& v : b1) v += 0;  // task indices are relative to the step's own task list
+    tsw.insert(tsw.end(), t1.begin(), t1.end());
+    bsw.insert(bsw.end(), b1.begin(), b1.end());
+  }
+  if (tmv.size() > P.plr_task_cap || trr.size() > P.plr_task_cap || tsw.size() > P.plr_task_cap ||
+      tleaf.size() > (size_t)nb * kPlrCap * P.ntiles)
+    return fail(PT_ERR_WORKSPACE, "PLR tables exceed their bounds");
+  c->ntask_mv = (int)tmv.size();
+  c->ntask_R = (int)trr.size();
+  PT_CUDA(cudaMemcpyAsync(c->d.lr_ord, lr.data(), lr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tile_ptr, tptr.data(), tptr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!tleaf.empty())
+    PT_CUDA(cudaMemcpyAsync(c->d.tile_leaf, tleaf.data(), tleaf.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!tmv.empty()) PT_CUDA(cudaMemcpyAsync(c->d.task_mv, tmv.data(), tmv.size() * sizeof(PlrTask), cudaMemcpyHostToDevice, s));
+  if (!trr.empty()) PT_CUDA(cudaMemcpyAsync(c->d.task_R, trr.data(), trr.size() * sizeof(PlrTask), cudaMemcpyHostToDevice, s));
+  if (!tsw.empty()) PT_CUDA(cudaMemcpyAsync(c->d.task_sw, tsw.data(), tsw.size() * sizeof(PlrTask), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tbase_mv, bmv.data(), bmv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tbase_R, brr.data(), brr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tbase_sw, bsw.data(), bsw.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (c->d.pool32) PT_CUDA(launch_pool_to_fp32(c->d.pool, c->d.pool32, (size_t)nb * P.nt * P.nt, s));
+  PT_CUDA(cudaStreamSynchronize(s));
   return PT_OK;
 }
 
@@ -427,7 +599,7 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
     return fail(PT_ERR_ARG, "workspaces must be 256-byte aligned");
   size_t need_p = 0;
   carve_persist(P, prm, nullptr, &need_p);
-  if (persistent_bytes < need_p || setup_bytes < setup_bytes_of(P))
+  if (persistent_bytes < need_p || setup_bytes < std::max(setup_bytes_of(P), plr_setup_bytes(P)))
     return fail(PT_ERR_WORKSPACE, "persistent or setup workspace too small");
   pt_ctx* c = new (std::nothrow) pt_ctx();
   if (!c) return fail(PT_ERR_ARG, "host allocation failed");
@@ -470,6 +642,10 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline phase: ") + cudaGetErrorString(e)));
   st = read_status(c);
   if (st != PT_OK) return bail(st);
+  if (P.plr) {
+    st = compress_blocks(c, setup, mv, rr, sw);
+    if (st != PT_OK) return bail(st);
+  }
   *out = c;
   return PT_OK;
 }
@@ -483,35 +659,65 @@ enum { kModeFP64 = 0, kModeFP32 = 1, kModeDF = 2 };
 
 bool mixed(const pt_ctx* c) { return c->prm.precision == PT_MIXED_FP32; }
 
-cudaError_t apply(pt_ctx* c, int mode, const ApplyRow* table, int nrows, int S, const cd* x, const cd* aux, cd* y,
-                  int rows_per_cta, double alpha, double beta) {
-  c->launches++;
+struct OpRef {
+  const ApplyRow* table;
+  int nrows;
+  const PlrTask* tasks;  // PLR projection tasks of this table (null without PLR)
+  int ntasks;
+  const int* tbase;
+};
+
+// Dense apply in the given arithmetic mode, or the PLR apply when the context
+// compresses its blocks and the caller asks for the working representation.
+cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, const cd* aux, cd* y, int rows_per_cta,
+                  double alpha, double beta, bool working) {
   const Plan& P = c->P;
+  if (working && P.plr) {
+    const bool fp32 = mode == kModeFP32;
+    c->launches += (op.ntasks > 0 ? 2 : 1);
+    return launch_plr_apply(fp32, P.nt, P.T4, fp32 ? P.ld32 : P.nt, op.table, op.nrows,
+                            fp32 ? static_cast<const void*>(c->d.blocks_hi) : static_cast<const void*>(c->d.blocks),
+                            fp32 ? static_cast<const void*>(c->d.pool32) : static_cast<const void*>(c->d.pool),
+                            c->d.leaves, op.tasks, op.ntasks, c->d.tile_ptr, c->d.tile_leaf, op.tbase, c->d.lr_ord,
+                            c->tbuf, P.rmax, x, aux, y, S, alpha, beta, c->stream);
+  }
+  c->launches++;
   if (mode == kModeFP64)
-    return launch_apply_mode(kModeFP64, P.nt, P.nt, P.T4, table, nrows, c->d.blocks, nullptr, x, aux, y, S,
+    return launch_apply_mode(kModeFP64, P.nt, P.nt, P.T4, op.table, op.nrows, c->d.blocks, nullptr, x, aux, y, S,
                              rows_per_cta, alpha, beta, c->stream);
-  return launch_apply_mode(mode, P.nt, P.ld32, P.T4, table, nrows, c->d.blocks_hi, c->d.blocks_lo, x, aux, y, S,
-                           rows_per_cta, alpha, beta, c->stream);
+  return launch_apply_mode(mode, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, c->d.blocks_lo, x, aux, y,
+                           S, rows_per_cta, alpha, beta, c->stream);
 }
 
-// y = P M x.  exact: FP64 blocks (true residual); otherwise the context's
-// working precision (double-float in the mixed form).
+OpRef op_matvec(pt_ctx* c) { return OpRef{c->d.tab_matvec, c->P.T4, c->d.task_mv, c->ntask_mv, c->d.tbase_mv}; }
+OpRef op_R(pt_ctx* c) { return OpRef{c->d.tab_R, c->P.T4, c->d.task_R, c->ntask_R, c->d.tbase_R}; }
+OpRef op_sweep(pt_ctx* c, int step) {
+  if (c->P.plr)
+    return OpRef{c->d.tab_sweep + 4 * step, 4, c->d.task_sw + c->sw_off[step], c->sw_cnt[step],
+                 c->d.tbase_sw + 16 * step};
+  return OpRef{c->d.tab_sweep + 4 * step, 4, nullptr, 0, nullptr};
+}
+
+// y = P M x.  exact: dense FP64 blocks (the true residual and the public
+// matvec); otherwise the working form: PLR blocks in FP64 when compressed,
+// else double-float (mixed) or FP64 dense blocks.
 cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y, bool exact = true) {
-  const int mode = (exact || !mixed(c)) ? kModeFP64 : kModeDF;
-  return apply(c, mode, c->d.tab_matvec, c->P.T4, S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0);
+  if (exact) return apply(c, kModeFP64, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, false);
+  const int mode = (c->P.plr || !mixed(c)) ? kModeFP64 : kModeDF;
+  return apply(c, mode, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, true);
 }
 
 // y = alpha R x + beta aux
 cudaError_t do_R(pt_ctx* c, int S, const cd* x, cd* y, int mode, double alpha = 1.0, double beta = 0.0,
-                 const cd* aux = nullptr) {
-  return apply(c, mode, c->d.tab_R, c->P.T4, S, x, aux, y, kApplyRowsWide, alpha, beta);
+                 const cd* aux = nullptr, bool working = false) {
+  return apply(c, mode, op_R(c), S, x, aux, y, kApplyRowsWide, alpha, beta, working);
 }
 
 // y = D^{-1} r (one launch per sweep step, down and up sweeps together); y must not alias r.
-cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode) {
+cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working = false) {
   const int steps = c->P.L - 1;
   for (int s = 0; s < steps; ++s) {
-    cudaError_t e = apply(c, mode, c->d.tab_sweep + 4 * s, 4, S, y, r, y, kApplyRowsSweep, 1.0, 0.0);
+    cudaError_t e = apply(c, mode, op_sweep(c, s), S, y, r, y, kApplyRowsSweep, 1.0, 0.0, working);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -521,10 +727,10 @@ cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode) {
 // Mixed form: FP32 blocks (the preconditioner only has to be approximate in flexible GMRES).
 cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* /*tmp2*/) {
   const int mode = mixed(c) ? kModeFP32 : kModeFP64;
-  cudaError_t e = do_Dinv(c, S, r, z, mode);
+  cudaError_t e = do_Dinv(c, S, r, z, mode, true);
   for (int it = 1; it < c->prm.gs_iters && e == cudaSuccess; ++it) {
-    e = do_R(c, S, z, tmp1, mode, -1.0, 1.0, r);  // tmp1 = r - R z
-    if (e == cudaSuccess) e = do_Dinv(c, S, tmp1, z, mode);
+    e = do_R(c, S, z, tmp1, mode, -1.0, 1.0, r, true);  // tmp1 = r - R z
+    if (e == cudaSuccess) e = do_Dinv(c, S, tmp1, z, mode, true);
   }
   return e;
 }
@@ -564,6 +770,36 @@ extern "C" pt_status pt_apply_matvec(pt_ctx* ctx, int32_t nsrc, const pt_c128* x
   return PT_OK;
 }
 
+extern "C" pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32_t nsrc, const pt_c128* x,
+                              pt_c128* y, void* scratch, size_t scratch_bytes) {
+  if (!ctx || !x || !y || x == y || which < 0 || which > 2) return fail(PT_ERR_ARG, "bad arguments");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  ctx->tbuf = B.tbuf;
+  const cd* xd = reinterpret_cast<const cd*>(x);
+  cd* yd = reinterpret_cast<cd*>(y);
+  const bool w = working != 0;
+  if (which == 0) {
+    PT_CUDA(do_matvec(ctx, nsrc, xd, yd, !w));
+  } else {
+    const int mode = (w && mixed(ctx)) ? kModeFP32 : kModeFP64;
+    if (which == 1) PT_CUDA(do_R(ctx, nsrc, xd, yd, mode, 1.0, 0.0, nullptr, w));
+    else PT_CUDA(do_Dinv(ctx, nsrc, xd, yd, mode, w));
+  }
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leaves) {
+  if (!ctx) return fail(PT_ERR_ARG, "ctx is NULL");
+  if (stored_entries) *stored_entries = (int64_t)ctx->plr_stored;
+  if (leaves) *leaves = ctx->plr_leaves;
+  return PT_OK;
+}
+
 extern "C" pt_status pt_apply_R(pt_ctx* ctx, int32_t nsrc, const pt_c128* x, pt_c128* y) {
   if (!ctx || !x || !y || nsrc < 1 || nsrc > ctx->prm.max_sources) return fail(PT_ERR_ARG, "bad arguments");
   PT_CUDA(do_R(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), kModeFP64));
@@ -586,6 +822,7 @@ extern "C" pt_status pt_apply_precond(pt_ctx* ctx, int32_t nsrc, const pt_c128* 
   pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
   if (st != PT_OK) return st;
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  ctx->tbuf = B.tbuf;
   PT_CUDA(do_precond(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), B.t, B.u1));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
@@ -642,6 +879,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
   const int m = c->prm.max_krylov;
   cudaStream_t s = c->stream;
   c->launches = 0;
+  c->tbuf = B.tbuf;
   std::vector<double> beta(S), rel(S, 1.0);
   std::vector<int> done(S, 0), kk(S, 0), total(S, 0);
   c->resid_h.assign(S, 0.0);

@@ -75,6 +75,17 @@ struct ExtractTask {
   int w;
 };
 
+// Partitioned low-rank leaf (Section 5.1) and projection task of the PLR apply.
+struct PlrLeaf {
+  int r0, c0, m, n, rank, kind;  // kind 0: dense, 1: low rank
+  long long off;                 // absolute offset in the factor pool:
+                                 //   low rank: (U S)^T at off (rank x m), (V^H)^T at off + rank*m (n x rank)
+                                 //   dense:    the leaf transposed at off (n x m)
+};
+struct PlrTask {
+  int row, term, leaf;
+};
+
 __device__ __forceinline__ cd cmul(cd a, cd b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 // a * b + c
 __device__ __forceinline__ cd cfma(cd a, cd b, cd c) {

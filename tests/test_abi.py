@@ -58,7 +58,7 @@ def _params(L_, **kw):
     from paper_1410_5910_gb300._lib import Params
 
     d = dict(nx=128, nz=128, npml=10, L=4, h=1 / 129, omega=81.0, pml_C=20.0, precision=0, gs_iters=2,
-             max_sources=1, max_krylov=30)
+             max_sources=1, max_krylov=30, plr=0, plr_eps=1e-9, plr_rmax=24)
     d.update(kw)
     return Params(**d)
 
@@ -83,7 +83,8 @@ def test_workspace_sizes_and_validation(L):
     assert L.pt_workspace_size(C.byref(p2), C.byref(a2), None, None) == 0
     assert a2.value > a.value  # FP32 copies of the blocks
     for bad in (dict(L=1), dict(h=0.0), dict(omega=-1.0), dict(gs_iters=0), dict(L=70), dict(npml=0),
-                dict(precision=7), dict(max_krylov=0)):
+                dict(precision=7), dict(max_krylov=0), dict(plr=1, plr_rmax=0), dict(plr=1, plr_rmax=40),
+                dict(plr=1, plr_eps=0.0)):
         assert L.pt_workspace_size(C.byref(_params(L, **bad)), None, None, None) == 1, bad
     assert b"" != L.pt_last_error()
     assert L.pt_status_string(5) == b"GMRES did not converge"
