@@ -62,10 +62,18 @@ typedef enum {
 } pt_status;
 
 typedef enum {
-  PT_FP64 = 0,      /* every block product in FP64                                   */
-  PT_MIXED_FP32 = 1 /* preconditioner (Algorithm 4) applies FP32 copies of the blocks;
-                       the GMRES matvec, Arnoldi, least squares and the true
-                       residual stay FP64 (flexible GMRES)                           */
+  PT_FP64 = 0,       /* every block product in FP64                                  */
+  PT_MIXED_FP32 = 1, /* preconditioner (Algorithm 4) applies FP32 copies of the
+                        blocks; the GMRES matvec and the local solves run in
+                        double-float (FP32 pairs, ~1e-14); Arnoldi, least squares
+                        and the explicit residual in FP64 (flexible GMRES)          */
+  PT_MIXED_TC = 2    /* for batches of sources: the block products run on the tensor
+                        cores with FP16 operands (power-of-two scales) and FP32
+                        accumulation - one pass in the preconditioner, the three-pass
+                        hi/lo split (~1e-5) in the GMRES matvec; the explicit residual
+                        between restart cycles is double-float (iterative refinement);
+                        local solves in double-float; Arnoldi and least squares in
+                        FP64.  pt_volume_residual gives an FP64 check.            */
 } pt_precision;
 
 typedef struct {
@@ -198,6 +206,14 @@ pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y
  * device trace vectors (nsrc of them), scratch >= solve_bytes. */
 pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32_t nsrc, const pt_c128* x, pt_c128* y,
                    void* scratch, size_t scratch_bytes);
+
+/* FP64 residual of the discrete Helmholtz equation of Section 2.1 on the
+ * whole extended grid: relres[s] = ||f_s - H u_s||_2 / ||f_s||_2 for nsrc
+ * volume fields u (device, layout of pt_solve's u) and sources f (device);
+ * relres host, nsrc doubles; scratch >= solve_bytes.  This is the check that
+ * does not depend on how the interface system was solved. */
+pt_status pt_volume_residual(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, const pt_c128* u, double* relres,
+                             void* scratch, size_t scratch_bytes);
 
 /* Size of the partitioned low-rank representation built by pt_create with
  * plr = 1 (Algorithm 5): complex entries stored (dense leaves count m n,

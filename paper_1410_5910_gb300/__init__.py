@@ -16,9 +16,10 @@ import math
 
 import torch
 
-from ._lib import PT_FP64, PT_MIXED_FP32, Params, PolarTraceError, check, lib
+from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, Params, PolarTraceError, check, lib
 
-__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "default_pml_strength", "layer_partition"]
+__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "default_pml_strength",
+           "layer_partition"]
 
 
 def default_pml_strength(c_max: float) -> float:
@@ -152,6 +153,16 @@ class PolarTrace:
         check(lib().pt_apply(self._ctx, w, int(working), x.shape[0], _ptr(x), _ptr(y), _ptr(self._scratch),
                              self._scratch.numel()), "pt_apply")
         return y
+
+    def volume_residual(self, f: torch.Tensor, u: torch.Tensor) -> list:
+        """FP64 ||f - H u|| / ||f|| per source on the extended grid (Section 2.1)."""
+        if f.dim() == 2:
+            f, u = f.unsqueeze(0), u.unsqueeze(0)
+        S = f.shape[0]
+        out = (C.c_double * S)()
+        check(lib().pt_volume_residual(self._ctx, S, _ptr(f), _ptr(u), out, _ptr(self._scratch),
+                                       self._scratch.numel()), "pt_volume_residual")
+        return list(out)
 
     def plr_stats(self):
         n = C.c_int64()

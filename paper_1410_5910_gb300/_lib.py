@@ -13,7 +13,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "libpolartrace.so")
 
-PT_FP64, PT_MIXED_FP32 = 0, 1
+PT_FP64, PT_MIXED_FP32, PT_MIXED_TC = 0, 1, 2
 STATUS = ["PT_OK", "PT_ERR_ARG", "PT_ERR_WORKSPACE", "PT_ERR_CUDA", "PT_ERR_SINGULAR", "PT_ERR_NOT_CONVERGED",
           "PT_ERR_TIMEOUT", "PT_ERR_NUMERIC"]
 
@@ -22,6 +22,7 @@ EXPORTS = [
     "pt_layer_partition", "pt_workspace_size", "pt_create", "pt_solve", "pt_solve_host", "pt_apply_matvec",
     "pt_apply_precond", "pt_apply_D_inverse", "pt_apply_R", "pt_rhs", "pt_get_block", "pt_last_solve_stats",
     "pt_destroy", "pt_status_string", "pt_last_error", "pt_rhs_noalloc", "pt_apply", "pt_plr_stats",
+    "pt_volume_residual",
 ]
 
 
@@ -66,6 +67,7 @@ def lib() -> C.CDLL:
     L.pt_rhs_noalloc.argtypes = [vp, i32, vp, vp]
     L.pt_apply.argtypes = [vp, i32, i32, i32, vp, vp, vp, sz]
     L.pt_plr_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
+    L.pt_volume_residual.argtypes = [vp, i32, vp, vp, C.POINTER(f64), vp, sz]
     L.pt_get_block.argtypes = [vp, i32, i32, i32, vp]
     L.pt_last_solve_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
     L.pt_destroy.argtypes = [vp]

@@ -4,9 +4,13 @@
 // permuted polarized jump system P M = D + R (Section 3.5); pt_solve runs
 // Algorithm 2 with flexible GMRES (right preconditioned by Algorithm 4,
 // Section 4.2) driven from the host, one stream synchronisation per iteration.
+#include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +50,17 @@ cudaError_t launch_plr_apply(bool, int, int, int, const ApplyRow*, int, const vo
                              const PlrTask*, int, const int*, const int*, const int*, const int*, cd*, int, const cd*,
                              const cd*, cd*, int, double, double, cudaStream_t);
 cudaError_t launch_pool_to_fp32(const cd*, cf*, size_t, cudaStream_t);
+bool tc_make_map(CUtensorMap*, const void*, size_t, int, int, int);
+int tc_ld(int nt);
+cudaError_t launch_tc_blocks(const cd*, size_t, int, int, double, __half*, __half*, cudaStream_t);
+cudaError_t launch_max_abs(const cd*, size_t, unsigned long long*, cudaStream_t);
+cudaError_t launch_tc_scale(const cd*, size_t, int, int, float*, float*, cudaStream_t);
+cudaError_t launch_tc_stage(const TcKey*, int, const cd*, int, int, int, int, const float*, __half*, __half*,
+                            cudaStream_t);
+cudaError_t launch_tc_apply(int, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&,
+                            const TcRow*, int, int, int, int, int, const float*, const cd*, const cd*, cd*, double,
+                            double, int*, cudaStream_t);
+cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
 cudaError_t launch_norm_scale(const cd*, size_t, int, double*, cd*, int, int, int, int, cd*, size_t,
@@ -107,6 +122,13 @@ struct Plan {
   int rmax = 0, oversample = 0, ntiles = 0;
   std::vector<int> plr_blocks;  // absolute block slots (layer * 16 + jk) that exist
   size_t plr_task_cap = 0;      // projection tasks of one operator table, upper bound
+  // tensor-core form
+  bool tc = false;
+  int ldtc = 0;                 // halves per row of the FP16 [Br Bi] rows
+  std::vector<TcRow> tc_mv, tc_R, tc_sw;
+  std::vector<TcKey> tk_mv, tk_R, tk_sw;
+  std::vector<int> tk_sw_off, tk_sw_cnt;
+  int tc_keys_max = 0;
 };
 
 pt_status make_plan(const pt_params* p, Plan& P) {
@@ -116,7 +138,9 @@ pt_status make_plan(const pt_params* p, Plan& P) {
   if (!(p->h > 0) || !(p->omega > 0) || !(p->pml_C >= 0) || !std::isfinite(p->h) || !std::isfinite(p->omega) ||
       !std::isfinite(p->pml_C))
     return fail(PT_ERR_ARG, "h and omega must be positive, pml_C non-negative, all finite");
-  if (p->precision != PT_FP64 && p->precision != PT_MIXED_FP32) return fail(PT_ERR_ARG, "unknown precision");
+  if (p->precision != PT_FP64 && p->precision != PT_MIXED_FP32 && p->precision != PT_MIXED_TC)
+    return fail(PT_ERR_ARG, "unknown precision");
+  if (p->precision == PT_MIXED_TC && p->plr) return fail(PT_ERR_ARG, "PT_MIXED_TC applies dense blocks (plr = 0)");
   if (p->gs_iters < 1 || p->gs_iters > 16) return fail(PT_ERR_ARG, "gs_iters must be in 1..16");
   if (p->max_sources < 1 || p->max_krylov < 1 || p->max_krylov > 512)
     return fail(PT_ERR_ARG, "max_sources >= 1 and 1 <= max_krylov <= 512");
@@ -222,6 +246,17 @@ struct Persist {
   int* tbase_R;
   PlrTask* task_sw;     // sweep steps, (L-1) x 4 rows
   int* tbase_sw;
+  // tensor-core form
+  __half* tc_ahi;       // [L * 16 * nt][ldtc]
+  __half* tc_alo;
+  TcRow* tcr_mv;
+  TcRow* tcr_R;
+  TcRow* tcr_sw;
+  TcKey* tck_mv;
+  TcKey* tck_R;
+  TcKey* tck_sw;
+  unsigned long long* tc_max;
+  double* m_ext;        // squared slowness on the extended grid (volume residual)
 };
 
 Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* bytes) {
@@ -234,10 +269,12 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
   q.Sinv = c.take<cd>(P.sinv_elems);
   const size_t bel = (size_t)P.L * 16 * P.nt * P.nt;
   q.blocks = c.take<cd>(bel);
-  if (p->precision == PT_MIXED_FP32) {
+  if (p->precision != PT_FP64) {  // FP32 / double-float copies of the blocks for the apply kernels
     const size_t bel32 = (size_t)P.L * 16 * P.nt * P.ld32;
     q.blocks_hi = c.take<cf>(bel32);
     q.blocks_lo = c.take<cf>(bel32);
+  }
+  if (p->precision != PT_FP64) {  // both mixed forms run the local solves in double-float
     q.sinv_hi = c.take<cf>(P.sinv_elems);
     q.sinv_lo = c.take<cf>(P.sinv_elems);
     q.w_hi = c.take<cf>(P.coef_elems);
@@ -266,6 +303,19 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
     q.task_sw = c.take<PlrTask>(P.plr_task_cap);
     q.tbase_sw = c.take<int>((size_t)(P.L - 1) * 16);
   }
+  if (P.tc) {
+    const size_t rowsA = (size_t)P.L * 16 * P.nt;
+    q.tc_ahi = c.take<__half>(rowsA * P.ldtc);
+    q.tc_alo = c.take<__half>(rowsA * P.ldtc);
+    q.tcr_mv = c.take<TcRow>(P.tc_mv.size());
+    q.tcr_R = c.take<TcRow>(P.tc_R.size());
+    q.tcr_sw = c.take<TcRow>(P.tc_sw.size());
+    q.tck_mv = c.take<TcKey>(P.tk_mv.size());
+    q.tck_R = c.take<TcKey>(P.tk_R.size());
+    q.tck_sw = c.take<TcKey>(P.tk_sw.size());
+    q.tc_max = c.take<unsigned long long>(4);
+  }
+  q.m_ext = c.take<double>((size_t)P.Nz * P.nt);
   if (bytes) *bytes = c.off;
   return q;
 }
@@ -296,6 +346,9 @@ struct SolveBufs {
   int* kk;
   cd *fdev, *udev;  // pt_solve_host staging
   cd* tbuf;         // PLR projections
+  __half *tc_bhi, *tc_blo;  // staged tensor-core operands
+  float *tc_scale, *tc_inv;
+  double* vres;     // volume residual partials
 };
 
 SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base, size_t* bytes) {
@@ -322,6 +375,14 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
   b.nrm = c.take<double>(S);
   b.kk = c.take<int>(S);
   b.tbuf = P.plr ? c.take<cd>((size_t)S * P.plr_task_cap * P.rmax) : nullptr;
+  if (P.tc) {
+    const size_t el = (size_t)P.tc_keys_max * 2 * S * P.ldtc;
+    b.tc_bhi = c.take<__half>(el);
+    b.tc_blo = c.take<__half>(el);
+    b.tc_scale = c.take<float>(S);
+    b.tc_inv = c.take<float>(S);
+  }
+  b.vres = c.take<double>((size_t)S + (size_t)S * 2 * 512);
   if (host_staging) {
     b.fdev = c.take<cd>((size_t)S * P.Nz * P.nt);
     b.udev = c.take<cd>((size_t)S * P.Nz * P.nt);
@@ -434,6 +495,62 @@ struct TableBuilder {
   }
 };
 
+// Tensor-core tables: the same terms with the staged input of each term
+// (sign * (x[in1] + x[in2])) deduplicated into keys.
+void tc_from(const ApplyRow* rows, int nrows, int nt, std::vector<TcRow>& out, std::vector<TcKey>& keys) {
+  std::map<std::tuple<int, int, int>, int> kmap;
+  for (int i = 0; i < nrows; ++i) {
+    const ApplyRow& a = rows[i];
+    TcRow r;
+    std::memset(&r, 0, sizeof(r));
+    r.out = a.out;
+    r.nterms = a.nterms;
+    for (int t = 0; t < a.nterms; ++t) {
+      const auto k = std::make_tuple(a.t[t].in1, a.t[t].in2, a.t[t].sign > 0 ? 1 : -1);
+      auto it = kmap.find(k);
+      int idx;
+      if (it == kmap.end()) {
+        idx = (int)keys.size();
+        kmap[k] = idx;
+        keys.push_back(TcKey{a.t[t].in1, a.t[t].in2, a.t[t].sign > 0 ? 1.0 : -1.0});
+      } else {
+        idx = it->second;
+      }
+      r.t[t] = TcTerm{a.t[t].block * nt, idx};
+    }
+    r.nid = a.nid;
+    for (int e = 0; e < a.nid; ++e) {
+      r.id_src[e] = a.id_src[e];
+      r.id_trace[e] = a.id_trace[e];
+      r.id_sign[e] = a.id_sign[e];
+    }
+    out.push_back(r);
+  }
+}
+
+pt_status full_plan(const pt_params* p, Plan& P) {
+  pt_status st = make_plan(p, P);
+  if (st != PT_OK) return st;
+  if (p->precision == PT_MIXED_TC) {
+    P.tc = true;
+    P.ldtc = tc_ld(P.nt);
+    TableBuilder tb{P};
+    auto mv = tb.matvec(), rr = tb.coupling(), sw = tb.sweeps();
+    tc_from(mv.data(), (int)mv.size(), P.nt, P.tc_mv, P.tk_mv);
+    tc_from(rr.data(), (int)rr.size(), P.nt, P.tc_R, P.tk_R);
+    for (int step = 0; step + 1 < P.L; ++step) {
+      std::vector<TcKey> k1;
+      tc_from(sw.data() + 4 * step, 4, P.nt, P.tc_sw, k1);
+      P.tk_sw_off.push_back((int)P.tk_sw.size());
+      P.tk_sw_cnt.push_back((int)k1.size());
+      P.tk_sw.insert(P.tk_sw.end(), k1.begin(), k1.end());
+      P.tc_keys_max = std::max(P.tc_keys_max, (int)k1.size());
+    }
+    P.tc_keys_max = std::max({P.tc_keys_max, (int)P.tk_mv.size(), (int)P.tk_R.size()});
+  }
+  return PT_OK;
+}
+
 }  // namespace
 
 struct pt_ctx {
@@ -450,6 +567,12 @@ struct pt_ctx {
   size_t plr_stored = 0;  // complex entries of the compressed representation
   int plr_leaves = 0;
   cd* tbuf = nullptr;     // projection buffer of the current call
+  // tensor-core form
+  int eA = 0;
+  CUtensorMap mapAhi, mapAlo, mapBhi, mapBlo;
+  int tc_bn = 0, tc_S = 0;
+  __half *tc_bhi = nullptr, *tc_blo = nullptr;
+  float *tc_scale = nullptr, *tc_inv = nullptr;
 };
 
 static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
@@ -465,7 +588,7 @@ extern "C" const char* pt_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" pt_status pt_layer_partition(const pt_params* prm, int32_t* row_start) {
   Plan P;
-  pt_status st = make_plan(prm, P);
+  pt_status st = full_plan(prm, P);
   if (st != PT_OK) return st;
   if (!row_start) return fail(PT_ERR_ARG, "row_start is NULL");
   for (int l = 0; l < P.L; ++l) row_start[l] = P.layers[l].start;
@@ -476,7 +599,7 @@ extern "C" pt_status pt_layer_partition(const pt_params* prm, int32_t* row_start
 extern "C" pt_status pt_workspace_size(const pt_params* prm, size_t* persistent_bytes, size_t* setup_bytes,
                                        size_t* solve_bytes) {
   Plan P;
-  pt_status st = make_plan(prm, P);
+  pt_status st = full_plan(prm, P);
   if (st != PT_OK) return st;
   size_t pb = 0, sb = 0;
   carve_persist(P, prm, nullptr, &pb);
@@ -587,12 +710,44 @@ static pt_status compress_blocks(pt_ctx* c, void* setup, const std::vector<Apply
   return PT_OK;
 }
 
+// FP16 [Br Bi] copies of the blocks with one power-of-two scale (max entry in
+// [2^9, 2^10)), the tensor-core tables, and the tensor maps of the block rows.
+static pt_status prepare_tc(pt_ctx* c) {
+  const Plan& P = c->P;
+  cudaStream_t s = c->stream;
+  const size_t nb = (size_t)P.L * 16 * P.nt * P.nt;
+  PT_CUDA(cudaMemsetAsync(c->d.tc_max, 0, sizeof(unsigned long long), s));
+  PT_CUDA(launch_max_abs(c->d.blocks, nb, c->d.tc_max, s));
+  unsigned long long bits = 0;
+  PT_CUDA(cudaMemcpyAsync(&bits, c->d.tc_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(cudaStreamSynchronize(s));
+  double mx;
+  std::memcpy(&mx, &bits, sizeof(mx));
+  int ex = 0;
+  if (mx > 0) std::frexp(mx, &ex);
+  c->eA = 10 - ex;
+  PT_CUDA(launch_tc_blocks(c->d.blocks, (size_t)P.L * 16 * P.nt, P.nt, P.ldtc, std::ldexp(1.0, c->eA), c->d.tc_ahi,
+                           c->d.tc_alo, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tcr_mv, P.tc_mv.data(), P.tc_mv.size() * sizeof(TcRow), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tcr_R, P.tc_R.data(), P.tc_R.size() * sizeof(TcRow), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tcr_sw, P.tc_sw.data(), P.tc_sw.size() * sizeof(TcRow), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tck_mv, P.tk_mv.data(), P.tk_mv.size() * sizeof(TcKey), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tck_R, P.tk_R.data(), P.tk_R.size() * sizeof(TcKey), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemcpyAsync(c->d.tck_sw, P.tk_sw.data(), P.tk_sw.size() * sizeof(TcKey), cudaMemcpyHostToDevice, s));
+  const size_t rowsA = (size_t)P.L * 16 * P.nt;
+  if (!tc_make_map(&c->mapAhi, c->d.tc_ahi, rowsA, P.ldtc, P.ldtc, 128) ||
+      !tc_make_map(&c->mapAlo, c->d.tc_alo, rowsA, P.ldtc, P.ldtc, 128))
+    return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the block rows");
+  PT_CUDA(cudaStreamSynchronize(s));
+  return PT_OK;
+}
+
 extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* persistent, size_t persistent_bytes,
                                void* setup, size_t setup_bytes, void* stream, pt_ctx** out) {
   if (!out) return fail(PT_ERR_ARG, "out is NULL");
   *out = nullptr;
   Plan P;
-  pt_status st = make_plan(prm, P);
+  pt_status st = full_plan(prm, P);
   if (st != PT_OK) return st;
   if (!c_ext || !persistent || !setup) return fail(PT_ERR_ARG, "NULL device pointer");
   if (((uintptr_t)persistent % kAlign) || ((uintptr_t)setup % kAlign))
@@ -624,6 +779,10 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
     return bail(fail(PT_ERR_CUDA, "copying operator tables"));
   // Algorithm 1
   if (launch_check_medium(c_ext, (size_t)P.Nz * P.nt, c->d.status, s) != cudaSuccess) return bail(fail(PT_ERR_CUDA, "check"));
+  if (cudaMemsetAsync(c->d.blocks, 0, (size_t)P.L * 16 * P.nt * P.nt * sizeof(cd), s) != cudaSuccess ||
+      cudaMemcpyAsync(c->d.m_ext, c_ext, (size_t)P.Nz * P.nt * sizeof(double), cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+    return bail(fail(PT_ERR_CUDA, "initialising the block storage"));
   st = read_status(c);
   if (st != PT_OK) return bail(st);
   cudaError_t e = launch_coef(g, c->d.layers, c_ext, c->d.W, c->d.E, s);
@@ -646,18 +805,42 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
     st = compress_blocks(c, setup, mv, rr, sw);
     if (st != PT_OK) return bail(st);
   }
+  if (P.tc) {
+    st = prepare_tc(c);
+    if (st != PT_OK) return bail(st);
+  }
   *out = c;
   return PT_OK;
 }
 
 extern "C" void pt_destroy(pt_ctx* ctx) { delete ctx; }
 
+// Point the context at this call's scratch: PLR projections and, in the
+// tensor-core form, the staged operands and their tensor maps.
+static pt_status bind_call(pt_ctx* c, const SolveBufs& B, int S) {
+  c->tbuf = B.tbuf;
+  if (!c->P.tc) return PT_OK;
+  c->tc_bhi = B.tc_bhi;
+  c->tc_blo = B.tc_blo;
+  c->tc_scale = B.tc_scale;
+  c->tc_inv = B.tc_inv;
+  const int two_s = 2 * S;
+  c->tc_bn = two_s <= 64 ? 64 : (two_s <= 128 ? 128 : 256);
+  const size_t rows = (size_t)c->P.tc_keys_max * two_s;
+  if (!tc_make_map(&c->mapBhi, B.tc_bhi, rows, c->P.ldtc, c->P.ldtc, c->tc_bn) ||
+      !tc_make_map(&c->mapBlo, B.tc_blo, rows, c->P.ldtc, c->P.ldtc, c->tc_bn))
+    return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the staged operands");
+  c->tc_S = S;
+  return PT_OK;
+}
+
 // ---- online building blocks ------------------------------------------------
 namespace {
 
-enum { kModeFP64 = 0, kModeFP32 = 1, kModeDF = 2 };
+enum { kModeFP64 = 0, kModeFP32 = 1, kModeDF = 2, kModeTC1 = 3, kModeTC3 = 4 };
 
-bool mixed(const pt_ctx* c) { return c->prm.precision == PT_MIXED_FP32; }
+bool mixed(const pt_ctx* c) { return c->prm.precision == PT_MIXED_FP32 || c->prm.precision == PT_MIXED_TC; }
+bool tcmode(const pt_ctx* c) { return c->prm.precision == PT_MIXED_TC; }
 
 struct OpRef {
   const ApplyRow* table;
@@ -665,6 +848,9 @@ struct OpRef {
   const PlrTask* tasks;  // PLR projection tasks of this table (null without PLR)
   int ntasks;
   const int* tbase;
+  const TcRow* tcr;      // tensor-core rows and staged-input keys (PT_MIXED_TC)
+  const TcKey* tck;
+  int nkeys;
 };
 
 // Dense apply in the given arithmetic mode, or the PLR apply when the context
@@ -672,6 +858,16 @@ struct OpRef {
 cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, const cd* aux, cd* y, int rows_per_cta,
                   double alpha, double beta, bool working) {
   const Plan& P = c->P;
+  if (mode == kModeTC1 || mode == kModeTC3) {
+    // staged inputs with the per-source scales set by tc_scale(), then the tensor-core products
+    const int npass = mode == kModeTC3 ? 3 : 1;
+    c->launches += 2;
+    cudaError_t e = launch_tc_stage(op.tck, op.nkeys, x, P.nt, P.T4, S, P.ldtc, c->tc_scale, c->tc_bhi,
+                                    npass == 3 ? c->tc_blo : nullptr, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_tc_apply(c->tc_bn, c->mapAhi, c->mapAlo, c->mapBhi, c->mapBlo, op.tcr, op.nrows, P.nt, P.T4, S,
+                           npass, c->tc_inv, x, aux, y, alpha, beta, c->d.status, c->stream);
+  }
   if (working && P.plr) {
     const bool fp32 = mode == kModeFP32;
     c->launches += (op.ntasks > 0 ? 2 : 1);
@@ -689,13 +885,33 @@ cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, cons
                            S, rows_per_cta, alpha, beta, c->stream);
 }
 
-OpRef op_matvec(pt_ctx* c) { return OpRef{c->d.tab_matvec, c->P.T4, c->d.task_mv, c->ntask_mv, c->d.tbase_mv}; }
-OpRef op_R(pt_ctx* c) { return OpRef{c->d.tab_R, c->P.T4, c->d.task_R, c->ntask_R, c->d.tbase_R}; }
+OpRef op_matvec(pt_ctx* c) {
+  return OpRef{c->d.tab_matvec, c->P.T4, c->d.task_mv, c->ntask_mv, c->d.tbase_mv, c->d.tcr_mv, c->d.tck_mv,
+               (int)c->P.tk_mv.size()};
+}
+OpRef op_R(pt_ctx* c) {
+  return OpRef{c->d.tab_R, c->P.T4, c->d.task_R, c->ntask_R, c->d.tbase_R, c->d.tcr_R, c->d.tck_R,
+               (int)c->P.tk_R.size()};
+}
 OpRef op_sweep(pt_ctx* c, int step) {
-  if (c->P.plr)
-    return OpRef{c->d.tab_sweep + 4 * step, 4, c->d.task_sw + c->sw_off[step], c->sw_cnt[step],
-                 c->d.tbase_sw + 16 * step};
-  return OpRef{c->d.tab_sweep + 4 * step, 4, nullptr, 0, nullptr};
+  OpRef o{c->d.tab_sweep + 4 * step, 4, nullptr, 0, nullptr, nullptr, nullptr, 0};
+  if (c->P.plr) {
+    o.tasks = c->d.task_sw + c->sw_off[step];
+    o.ntasks = c->sw_cnt[step];
+    o.tbase = c->d.tbase_sw + 16 * step;
+  }
+  if (c->P.tc) {
+    o.tcr = c->d.tcr_sw + 4 * step;
+    o.tck = c->d.tck_sw + c->P.tk_sw_off[step];
+    o.nkeys = c->P.tk_sw_cnt[step];
+  }
+  return o;
+}
+
+// Per-source FP16 scales of a tensor-core apply, from the vector `ref`.
+cudaError_t tc_scale(pt_ctx* c, int S, const cd* ref) {
+  c->launches++;
+  return launch_tc_scale(ref, c->P.N, S, c->eA, c->tc_scale, c->tc_inv, c->stream);
 }
 
 // y = P M x.  exact: dense FP64 blocks (the true residual and the public
@@ -703,6 +919,11 @@ OpRef op_sweep(pt_ctx* c, int step) {
 // else double-float (mixed) or FP64 dense blocks.
 cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y, bool exact = true) {
   if (exact) return apply(c, kModeFP64, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, false);
+  if (tcmode(c)) {
+    cudaError_t e = tc_scale(c, S, x);
+    if (e != cudaSuccess) return e;
+    return apply(c, kModeTC3, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, true);
+  }
   const int mode = (c->P.plr || !mixed(c)) ? kModeFP64 : kModeDF;
   return apply(c, mode, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, true);
 }
@@ -710,12 +931,21 @@ cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y, bool exact = true) {
 // y = alpha R x + beta aux
 cudaError_t do_R(pt_ctx* c, int S, const cd* x, cd* y, int mode, double alpha = 1.0, double beta = 0.0,
                  const cd* aux = nullptr, bool working = false) {
+  if (mode == kModeTC1 || mode == kModeTC3) {
+    cudaError_t e = tc_scale(c, S, x);
+    if (e != cudaSuccess) return e;
+  }
   return apply(c, mode, op_R(c), S, x, aux, y, kApplyRowsWide, alpha, beta, working);
 }
 
 // y = D^{-1} r (one launch per sweep step, down and up sweeps together); y must not alias r.
 cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working = false) {
   const int steps = c->P.L - 1;
+  if (mode == kModeTC1 || mode == kModeTC3) {
+    // one scale per source for the whole sweep, from the right-hand side
+    cudaError_t e = tc_scale(c, S, r);
+    if (e != cudaSuccess) return e;
+  }
   for (int s = 0; s < steps; ++s) {
     cudaError_t e = apply(c, mode, op_sweep(c, s), S, y, r, y, kApplyRowsSweep, 1.0, 0.0, working);
     if (e != cudaSuccess) return e;
@@ -726,7 +956,7 @@ cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working
 // Algorithm 4: z = D^{-1} r; repeat n_it - 1 times z = D^{-1}(r - R z).
 // Mixed form: FP32 blocks (the preconditioner only has to be approximate in flexible GMRES).
 cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* /*tmp2*/) {
-  const int mode = mixed(c) ? kModeFP32 : kModeFP64;
+  const int mode = tcmode(c) ? kModeTC1 : (mixed(c) ? kModeFP32 : kModeFP64);
   cudaError_t e = do_Dinv(c, S, r, z, mode, true);
   for (int it = 1; it < c->prm.gs_iters && e == cudaSuccess; ++it) {
     e = do_R(c, S, z, tmp1, mode, -1.0, 1.0, r, true);  // tmp1 = r - R z
@@ -738,9 +968,11 @@ cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* /*tmp
 cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xtr, cd* out, const SolveBufs& B) {
   c->launches++;
   const Plan& P = c->P;
-  if (mixed(c))
+  if (mixed(c)) {
+    if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
     return launch_layer_solve_df(mode, P.g, c->d.layers, c->d.sinv_hi, c->d.sinv_lo, c->d.w_hi, c->d.w_lo, c->d.e_hi,
                                  c->d.e_lo, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
+  }
   return launch_layer_solve2(mode, false, P.g, c->d.layers, c->d.Sinv, nullptr, nullptr, c->d.W, c->d.E, f, xtr,
                              B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
 }
@@ -778,17 +1010,33 @@ extern "C" pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32
   pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
   if (st != PT_OK) return st;
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
-  ctx->tbuf = B.tbuf;
+  st = bind_call(ctx, B, nsrc);
+  if (st != PT_OK) return st;
   const cd* xd = reinterpret_cast<const cd*>(x);
   cd* yd = reinterpret_cast<cd*>(y);
   const bool w = working != 0;
   if (which == 0) {
     PT_CUDA(do_matvec(ctx, nsrc, xd, yd, !w));
   } else {
-    const int mode = (w && mixed(ctx)) ? kModeFP32 : kModeFP64;
+    const int mode = (w && tcmode(ctx)) ? kModeTC1 : ((w && mixed(ctx)) ? kModeFP32 : kModeFP64);
     if (which == 1) PT_CUDA(do_R(ctx, nsrc, xd, yd, mode, 1.0, 0.0, nullptr, w));
     else PT_CUDA(do_Dinv(ctx, nsrc, xd, yd, mode, w));
   }
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_volume_residual(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, const pt_c128* u,
+                                        double* relres, void* scratch, size_t scratch_bytes) {
+  if (!ctx || !f || !u || !relres) return fail(PT_ERR_ARG, "bad arguments");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  PT_CUDA(launch_volume_residual(ctx->P.g, ctx->d.m_ext, reinterpret_cast<const cd*>(f),
+                                 reinterpret_cast<const cd*>(u), nsrc, B.vres, ctx->stream));
+  PT_CUDA(cudaMemcpyAsync(relres, B.vres, nsrc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
 }
@@ -822,7 +1070,8 @@ extern "C" pt_status pt_apply_precond(pt_ctx* ctx, int32_t nsrc, const pt_c128* 
   pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
   if (st != PT_OK) return st;
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
-  ctx->tbuf = B.tbuf;
+  st = bind_call(ctx, B, nsrc);
+  if (st != PT_OK) return st;
   PT_CUDA(do_precond(ctx, nsrc, reinterpret_cast<const cd*>(x), reinterpret_cast<cd*>(y), B.t, B.u1));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
@@ -879,7 +1128,10 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
   const int m = c->prm.max_krylov;
   cudaStream_t s = c->stream;
   c->launches = 0;
-  c->tbuf = B.tbuf;
+  {
+    pt_status bs = bind_call(c, B, S);
+    if (bs != PT_OK) return bs;
+  }
   std::vector<double> beta(S), rel(S, 1.0);
   std::vector<int> done(S, 0), kk(S, 0), total(S, 0);
   c->resid_h.assign(S, 0.0);
@@ -946,8 +1198,11 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     PT_CUDA(cudaMemcpyAsync(B.kk, kk.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
     c->launches += 2;
     PT_CUDA(launch_lsq_combine(S, m, B.kk, B.H, B.g, B.y, B.Z, N, B.x, s));
-    // explicit residual r = P b - P M x
-    PT_CUDA(do_matvec(c, S, B.x, B.t));
+    // explicit residual r = P b - P M x between restart cycles (iterative refinement): FP64 blocks,
+    // or in PT_MIXED_TC the double-float product (~1e-14) on the FP32 pipes, since the tensor-core
+    // matvec of the inner cycles is only ~1e-5 accurate
+    if (tcmode(c)) PT_CUDA(apply(c, kModeDF, op_matvec(c), S, B.x, nullptr, B.t, kApplyRowsWide, 1.0, 0.0, false));
+    else PT_CUDA(do_matvec(c, S, B.x, B.t));
     c->launches += 2;
     PT_CUDA(launch_sub(B.b, B.t, B.w, S * N, s));
     PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, s));

@@ -86,6 +86,23 @@ struct PlrTask {
   int row, term, leaf;
 };
 
+// Tensor-core apply: one output trace of a batched operator (see pt_tc.cu).
+struct TcTerm {
+  int a_row0;  // first row of the block in the stacked FP16 block tensor (slot * n_t)
+  int key;     // staged operand: rows [key * 2S, (key + 1) * 2S) of the stacked operand tensor
+};
+struct TcRow {
+  int out, nterms;
+  TcTerm t[4];
+  int nid;
+  int id_src[2], id_trace[2];
+  double id_sign[2];
+};
+struct TcKey {  // staged input sign * (x[in1] + x[in2])
+  int in1, in2;
+  double sign;
+};
+
 __device__ __forceinline__ cd cmul(cd a, cd b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 // a * b + c
 __device__ __forceinline__ cd cfma(cd a, cd b, cd c) {

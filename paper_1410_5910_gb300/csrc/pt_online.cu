@@ -185,9 +185,85 @@ __global__ void sub_kernel(const cd* __restrict__ a, const cd* __restrict__ b, c
 }
 
 // ---------------------------------------------------------------------------
+// FP64 residual of the global discrete Helmholtz equation (Section 2.1)
+// ---------------------------------------------------------------------------
+constexpr int kVresBlocks = 512;
+
+// partial[(s * kVresBlocks + b) * 2 + {0, 1}] = sum over the block's points of |f - H u|^2 and |f|^2
+__global__ void __launch_bounds__(256) volres_kernel(Geometry g, const double* __restrict__ c_ext,
+                                                     const cd* __restrict__ f, const cd* __restrict__ u,
+                                                     double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const size_t np = (size_t)g.Nz * g.nt;
+  const cd* us = u + s * np;
+  const cd* fs = f + s * np;
+  const double ih2 = 1.0 / (g.h * g.h);
+  double rr = 0.0, ff = 0.0;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < np; idx += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / g.nt), p = (int)(idx - (size_t)q * g.nt);
+    const cd ax = pml_alpha(p, g.nt, g), axp = pml_alpha(p + 0.5, g.nt, g), axm = pml_alpha(p - 0.5, g.nt, g);
+    const cd az = pml_alpha(q, g.Nz, g), azp = pml_alpha(q + 0.5, g.Nz, g), azm = pml_alpha(q - 0.5, g.Nz, g);
+    const double c = c_ext[idx];
+    const double m = 1.0 / (c * c);
+    const cd sx = cmul(ax, cadd(axp, axm)), sz = cmul(az, cadd(azp, azm));
+    const cd center = make_double2((sx.x + sz.x) * ih2 - g.omega * g.omega * m, (sx.y + sz.y) * ih2);
+    cd hu = cmul(center, us[idx]);
+    if (p > 0) hu = cadd(hu, cmul(cscale(cmul(ax, axm), -ih2), us[idx - 1]));
+    if (p < g.nt - 1) hu = cadd(hu, cmul(cscale(cmul(ax, axp), -ih2), us[idx + 1]));
+    if (q > 0) hu = cadd(hu, cmul(cscale(cmul(az, azm), -ih2), us[idx - g.nt]));
+    if (q < g.Nz - 1) hu = cadd(hu, cmul(cscale(cmul(az, azp), -ih2), us[idx + g.nt]));
+    const cd r = csub(fs[idx], hu);
+    rr += cabs2(r);
+    ff += cabs2(fs[idx]);
+  }
+  __shared__ double red[2][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    ff += __shfl_down_sync(0xffffffffu, ff, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = rr;
+    red[1][threadIdx.x >> 5] = ff;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partial[((size_t)s * gridDim.x + blockIdx.x) * 2] = a;
+    partial[((size_t)s * gridDim.x + blockIdx.x) * 2 + 1] = b;
+  }
+}
+
+__global__ void volres_final_kernel(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  const int s = blockIdx.x;
+  double a = 0, b = 0;
+  for (int k = threadIdx.x; k < nblk; k += 32) {
+    a += partial[((size_t)s * nblk + k) * 2];
+    b += partial[((size_t)s * nblk + k) * 2 + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (threadIdx.x == 0) out[s] = b > 0 ? sqrt(a / b) : sqrt(a);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 int dot_chunks(size_t N) { return (int)((N + kDotChunk - 1) / kDotChunk); }
+
+// work: at least nsrc + 2 * nsrc * 512 doubles; out = work[0 .. nsrc)
+cudaError_t launch_volume_residual(const Geometry& g, const double* c_ext, const cd* f, const cd* u, int nsrc,
+                                   double* work, cudaStream_t s) {
+  double* partial = work + nsrc;
+  volres_kernel<<<dim3(kVresBlocks, nsrc), 256, 0, s>>>(g, c_ext, f, u, partial);
+  volres_final_kernel<<<nsrc, 32, 0, s>>>(partial, kVresBlocks, work);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dots(const cd* V, int nsrc, size_t N, const cd* w, int nvec, cd* partial, cd* coef,
                         int coef_stride, cd* H, int hrows, int hcols, int col, cudaStream_t s) {
