@@ -221,6 +221,14 @@ pt_status pt_volume_residual(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, const 
  * allowed).  Zero when the context keeps dense blocks. */
 pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leaves);
 
+/* Tuning options of a context (they change speed, not results beyond
+ * rounding).  PT_OPT_LAYER_GROUP: sources per CTA of the source-batched
+ * local solves of PT_MIXED_TC (Algorithm 2 and the reconstruction of
+ * Section 2.3): 0 = chosen from L and nsrc (default), or 8, 16, 32.
+ * PT_ERR_ARG for an unknown option or value. */
+enum { PT_OPT_LAYER_GROUP = 1 };
+pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
+
 /* Copy the interface Green's matrix G^l(z_j, z_k) / h (the block that the
  * incomplete Green's integrals of Definition 2 multiply) to dst (device,
  * n_t * n_t pt_c128, row-major, row = target node, column = source node).

@@ -16,9 +16,9 @@ import math
 
 import torch
 
-from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, Params, PolarTraceError, check, lib
+from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, Params, PolarTraceError, check, lib
 
-__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "default_pml_strength",
+__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "default_pml_strength",
            "layer_partition"]
 
 
@@ -163,6 +163,10 @@ class PolarTrace:
         check(lib().pt_volume_residual(self._ctx, S, _ptr(f), _ptr(u), out, _ptr(self._scratch),
                                        self._scratch.numel()), "pt_volume_residual")
         return list(out)
+
+    def set_option(self, option: int, value: int) -> None:
+        """Tuning option (PT_OPT_LAYER_GROUP: sources per CTA of the batched local solves)."""
+        check(lib().pt_set_option(self._ctx, int(option), int(value)), "pt_set_option")
 
     def plr_stats(self):
         n = C.c_int64()

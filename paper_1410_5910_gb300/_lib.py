@@ -22,8 +22,9 @@ EXPORTS = [
     "pt_layer_partition", "pt_workspace_size", "pt_create", "pt_solve", "pt_solve_host", "pt_apply_matvec",
     "pt_apply_precond", "pt_apply_D_inverse", "pt_apply_R", "pt_rhs", "pt_get_block", "pt_last_solve_stats",
     "pt_destroy", "pt_status_string", "pt_last_error", "pt_rhs_noalloc", "pt_apply", "pt_plr_stats",
-    "pt_volume_residual",
+    "pt_volume_residual", "pt_set_option",
 ]
+PT_OPT_LAYER_GROUP = 1
 
 
 class Params(C.Structure):

@@ -60,6 +60,8 @@ cudaError_t launch_tc_stage(const TcKey*, int, const cd*, int, int, int, int, co
 cudaError_t launch_tc_apply(int, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&,
                             const TcRow*, int, int, int, int, int, const float*, const cd*, const cd*, cd*, double,
                             double, int*, cudaStream_t);
+cudaError_t launch_layer_solve_batch(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
+                                     const cd*, const cd*, cd*, cd*, const int*, int, int, cudaStream_t);
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
@@ -355,7 +357,10 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
   Carver c(base);
   SolveBufs b{};
   const size_t N = P.N;
-  b.Y = c.take<cd>((size_t)S * P.L * P.nt * P.nloc_max);
+  // forward iterates of the local solves; the source-batched solves of the tensor-core
+  // form keep them in complex64 per (layer, group of up to 32 sources): room for
+  // round_up(S, 32) sources in half the bytes
+  b.Y = c.take<cd>((size_t)(P.tc ? std::max(S, 16) : S) * P.L * P.nt * P.nloc_max);
   b.nzflag = c.take<int>((size_t)S * P.L);
   b.b = c.take<cd>(S * N);
   b.x = c.take<cd>(S * N);
@@ -573,6 +578,7 @@ struct pt_ctx {
   int tc_bn = 0, tc_S = 0;
   __half *tc_bhi = nullptr, *tc_blo = nullptr;
   float *tc_scale = nullptr, *tc_inv = nullptr;
+  int opt_layer_group = 0;  // PT_OPT_LAYER_GROUP
 };
 
 static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
@@ -968,6 +974,11 @@ cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* /*tmp
 cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xtr, cd* out, const SolveBufs& B) {
   c->launches++;
   const Plan& P = c->P;
+  if (tcmode(c)) {  // many sources: FP32 local solves, one Sinv read per group of sources
+    if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;
+    return launch_layer_solve_batch(mode, P.g, c->d.layers, P.nloc_max, c->d.sinv_hi, c->d.w_hi, c->d.e_hi, f, xtr,
+                                    B.Y, out, B.nzflag, S, c->opt_layer_group, c->stream);
+  }
   if (mixed(c)) {
     if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
     return launch_layer_solve_df(mode, P.g, c->d.layers, c->d.sinv_hi, c->d.sinv_lo, c->d.w_hi, c->d.w_lo, c->d.e_hi,
@@ -1039,6 +1050,16 @@ extern "C" pt_status pt_volume_residual(pt_ctx* ctx, int32_t nsrc, const pt_c128
   PT_CUDA(cudaMemcpyAsync(relres, B.vres, nsrc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));
   return PT_OK;
+}
+
+extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
+  if (!ctx) return fail(PT_ERR_ARG, "ctx is NULL");
+  if (option == PT_OPT_LAYER_GROUP) {
+    if (value != 0 && value != 8 && value != 16 && value != 32) return fail(PT_ERR_ARG, "layer group must be 0, 8, 16 or 32");
+    ctx->opt_layer_group = value;
+    return PT_OK;
+  }
+  return fail(PT_ERR_ARG, "unknown option");
 }
 
 extern "C" pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leaves) {
