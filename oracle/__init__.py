@@ -24,6 +24,10 @@ krylov          Section 4.2: GMRES (left preconditioned) and flexible GMRES
                 Givens rotations.
 solver          Algorithm 2 end to end with the polarized system.
 plr             Section 5.1: Algorithms 5 and 6 and the flattened leaf form.
+learned         Not in the paper: the learned correction N_theta of the
+                preconditioner used inside flexible GMRES (Section 4.2) -
+                forward pass, loss, exact gradient, trace/feature maps and
+                the defect targets e - K^{-1} r of Algorithm 4.
 
 Parity status: every function here is pinned by a test in
 ``tests/test_oracle_*.py`` against an identity the paper proves, a closed
