@@ -72,8 +72,10 @@ typedef enum {
                         accumulation - one pass in the preconditioner, the three-pass
                         hi/lo split (~1e-5) in the GMRES matvec; the explicit residual
                         between restart cycles is double-float (iterative refinement);
-                        local solves in double-float; Arnoldi and least squares in
-                        FP64.  pt_volume_residual gives an FP64 check.            */
+                        local solves (right-hand side, reconstruction) in FP32 with
+                        the FP64 factors rounded to complex64, batched over groups
+                        of sources; Arnoldi and least squares in FP64.
+                        pt_volume_residual gives an FP64 check.                   */
 } pt_precision;
 
 typedef struct {
@@ -93,6 +95,9 @@ typedef struct {
   double plr_eps;     /* relative threshold: a node is a leaf when sigma_{r_max+1}
                          < plr_eps * sigma_1 of its whole block                      */
   int32_t plr_rmax;   /* r_max, 1 .. 31                                              */
+  int32_t learned;    /* 1: reserve the solve-scratch buffers of the learned
+                         preconditioner correction (pt_set_correction,
+                         PT_OPT_LEARNED); 0: none                                    */
 } pt_params;
 
 /* Layer partition used by the library (Section 2.2): the first (N_z mod L)
@@ -225,9 +230,59 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * rounding).  PT_OPT_LAYER_GROUP: sources per CTA of the source-batched
  * local solves of PT_MIXED_TC (Algorithm 2 and the reconstruction of
  * Section 2.3): 0 = chosen from L and nsrc (default), or 8, 16, 32.
+ * PT_OPT_LEARNED: 1 = flexible GMRES adds the learned correction to the
+ * preconditioner (needs learned = 1 at pt_create and weights, see below),
+ * 0 = plain Algorithm 4 (default).
  * PT_ERR_ARG for an unknown option or value. */
-enum { PT_OPT_LAYER_GROUP = 1 };
+enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2 };
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
+
+/* ---- learned preconditioner correction (not in the paper) ------------------
+ * A network N_theta on interface traces corrects the Gauss-Seidel
+ * preconditioner K^{-1} of Algorithm 4 inside flexible GMRES (Section 4.2):
+ * z = K^{-1} v + N_theta(v).  For one source, v (a permuted residual, the
+ * vectors GMRES preconditions) is divided by its RMS s; each interface i
+ * gives one sequence of n_t positions with 8 channels, Re/Im of the rows
+ * 2i, 2i+1, T+2i, T+2i+1 (T = 2(L-1)); the network is
+ *   h1 = b1 + W1 * x   (1D cross-correlation over x, kernel 7, zero padding, 8 -> 256)
+ *   h2 = b2 + W2 g(h1), h3 = b3 + W3 g(h2), y = b4 + W4 g(h3)
+ * with g(x) = x/2 (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3))); y (8 channels)
+ * times s is added to the same slots of z.  Weights are used in BF16,
+ * activations and accumulation in FP32; training keeps an FP32 master copy
+ * and Adam moments.  Flat FP32 parameter order:
+ *   W1 (256, 8, 7) | b1 (256) | W2 (256, 256) | b2 | W3 (256, 256) | b3 | W4 (8, 256) | b4 (8).
+ * Features and outputs in the calls below are channel-major float arrays
+ * x[c * P + pos], pos = seq * n_t + position, P = nseq * n_t (device). */
+pt_status pt_correction_nparams(int64_t* nparams);
+/* Weights from / to host memory (nparams floats).  Setting resets Adam. */
+pt_status pt_set_correction(pt_ctx* ctx, const float* params, int64_t nparams);
+pt_status pt_get_correction(const pt_ctx* ctx, float* params, int64_t nparams);
+/* Device scratch for pt_correction_forward / pt_correction_grad on nseq sequences. */
+pt_status pt_correction_scratch_bytes(const pt_ctx* ctx, int32_t nseq, size_t* bytes);
+/* y = N_theta(x) on raw features (no RMS scaling): x, y device, 8 x P floats. */
+pt_status pt_correction_forward(pt_ctx* ctx, int32_t nseq, const float* x, float* y, void* scratch,
+                                size_t scratch_bytes);
+/* Loss 0.5 mean (N_theta(x) - t)^2 (host double) and its gradient with respect
+ * to the parameters (device, nparams floats, overwritten), at the BF16 weights. */
+pt_status pt_correction_grad(pt_ctx* ctx, int32_t nseq, const float* x, const float* t, double* loss, float* grad,
+                             void* scratch, size_t scratch_bytes);
+/* Scratch for pt_train_correction with npairs pairs and minibatches of batch pairs. */
+pt_status pt_train_bytes(const pt_ctx* ctx, int32_t npairs, int32_t batch, size_t* bytes);
+/* Train on solver-generated pairs: r[p] a permuted residual and e[p] the error
+ * it belongs to ((P M) e = r, e.g. e = x* - x_k and r = P b - P M x_k of a
+ * GMRES iterate), both device, npairs x 4(L-1) x n_t complex.  Targets are
+ * (e - K^{-1} r) / RMS(r) with K^{-1} at the context's precision; Adam with
+ * learning rate lr for `steps` minibatches of `batch` pairs drawn with `seed`.
+ * Starts from the current weights (a seeded default initialisation when none
+ * were set).  loss_first / loss_last (host, NULL allowed): loss of the first
+ * and the last minibatch.  scratch >= pt_train_bytes. */
+pt_status pt_train_correction(pt_ctx* ctx, int32_t npairs, const pt_c128* r, const pt_c128* e, int32_t steps,
+                              int32_t batch, double lr, uint64_t seed, double* loss_first, double* loss_last,
+                              void* scratch, size_t scratch_bytes);
+/* z = N_theta(v) for nsrc permuted residuals (device); needs learned = 1 and
+ * weights; scratch >= solve_bytes. */
+pt_status pt_apply_correction(pt_ctx* ctx, int32_t nsrc, const pt_c128* v, pt_c128* z, void* scratch,
+                              size_t scratch_bytes);
 
 /* Copy the interface Green's matrix G^l(z_j, z_k) / h (the block that the
  * incomplete Green's integrals of Definition 2 multiply) to dst (device,

@@ -16,9 +16,9 @@ import math
 
 import torch
 
-from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, Params, PolarTraceError, check, lib
+from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, PT_OPT_LEARNED, Params, PolarTraceError, check, lib
 
-__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "default_pml_strength",
+__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "default_pml_strength",
            "layer_partition"]
 
 
@@ -28,9 +28,9 @@ def default_pml_strength(c_max: float) -> float:
 
 
 def _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr=0, plr_eps=1e-9,
-            plr_rmax=24) -> Params:
+            plr_rmax=24, learned=0) -> Params:
     return Params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr, plr_eps,
-                  plr_rmax)
+                  plr_rmax, learned)
 
 
 def layer_partition(nx, nz, npml, L) -> list:
@@ -51,7 +51,7 @@ class PolarTrace:
     def __init__(self, nx: int, nz: int, npml: int, L: int, h: float, omega: float, c_ext: torch.Tensor,
                  pml_C: float | None = None, precision: int = PT_FP64, gs_iters: int = 2, max_sources: int = 1,
                  max_krylov: int = 40, stream: torch.cuda.Stream | None = None, plr: bool = False,
-                 plr_eps: float = 1e-9, plr_rmax: int = 24):
+                 plr_eps: float = 1e-9, plr_rmax: int = 24, learned: bool = False):
         if not (c_ext.is_cuda and c_ext.dtype == torch.float64 and c_ext.is_contiguous()):
             raise ValueError("c_ext must be a contiguous float64 CUDA tensor of shape (N_z, n_t)")
         self.nx, self.nz, self.npml, self.L = nx, nz, npml, L
@@ -61,7 +61,7 @@ class PolarTrace:
         if pml_C is None:
             pml_C = default_pml_strength(float(c_ext.max()))
         self.params = _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov,
-                              int(plr), plr_eps, plr_rmax)
+                              int(plr), plr_eps, plr_rmax, int(learned))
         self.max_sources, self.max_krylov = max_sources, max_krylov
         self.device = c_ext.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -163,6 +163,65 @@ class PolarTrace:
         check(lib().pt_volume_residual(self._ctx, S, _ptr(f), _ptr(u), out, _ptr(self._scratch),
                                        self._scratch.numel()), "pt_volume_residual")
         return list(out)
+
+    # ---- learned correction of the preconditioner ------------------------------
+    @staticmethod
+    def correction_nparams() -> int:
+        n = C.c_int64()
+        check(lib().pt_correction_nparams(C.byref(n)), "pt_correction_nparams")
+        return n.value
+
+    def set_correction(self, theta) -> None:
+        """Network weights (flat float32, the order of include/polartrace.h) from host memory."""
+        t = torch.as_tensor(theta, dtype=torch.float32).contiguous().cpu()
+        check(lib().pt_set_correction(self._ctx, t.data_ptr(), t.numel()), "pt_set_correction")
+
+    def get_correction(self) -> torch.Tensor:
+        t = torch.empty(self.correction_nparams(), dtype=torch.float32)
+        check(lib().pt_get_correction(self._ctx, t.data_ptr(), t.numel()), "pt_get_correction")
+        return t
+
+    def _nn_scratch(self, nseq: int) -> torch.Tensor:
+        b = C.c_size_t()
+        check(lib().pt_correction_scratch_bytes(self._ctx, nseq, C.byref(b)), "pt_correction_scratch_bytes")
+        return torch.empty(max(b.value, 256), dtype=torch.uint8, device=self.device)
+
+    def correction_forward(self, x: torch.Tensor) -> torch.Tensor:
+        """N_theta on raw features x (8, nseq * n_t) float32 CUDA."""
+        nseq = x.shape[1] // self.nt
+        y = torch.empty_like(x)
+        sc = self._nn_scratch(nseq)
+        check(lib().pt_correction_forward(self._ctx, nseq, _ptr(x), _ptr(y), _ptr(sc), sc.numel()),
+              "pt_correction_forward")
+        return y
+
+    def correction_grad(self, x: torch.Tensor, t: torch.Tensor):
+        """(loss, gradient) of 0.5 mean (N_theta(x) - t)^2 at the BF16 weights."""
+        nseq = x.shape[1] // self.nt
+        g = torch.empty(self.correction_nparams(), dtype=torch.float32, device=self.device)
+        sc = self._nn_scratch(nseq)
+        loss = C.c_double()
+        check(lib().pt_correction_grad(self._ctx, nseq, _ptr(x), _ptr(t), C.byref(loss), _ptr(g), _ptr(sc),
+                                       sc.numel()), "pt_correction_grad")
+        return loss.value, g
+
+    def train_correction(self, r: torch.Tensor, e: torch.Tensor, steps: int, batch: int, lr: float = 1e-3,
+                         seed: int = 0):
+        """Adam on (residual, error) pairs; returns (first, last) minibatch loss."""
+        n = r.shape[0]
+        b = C.c_size_t()
+        check(lib().pt_train_bytes(self._ctx, n, batch, C.byref(b)), "pt_train_bytes")
+        sc = torch.empty(max(b.value, 256), dtype=torch.uint8, device=self.device)
+        l0, l1 = C.c_double(), C.c_double()
+        check(lib().pt_train_correction(self._ctx, n, _ptr(r), _ptr(e), steps, batch, lr, seed, C.byref(l0),
+                                        C.byref(l1), _ptr(sc), sc.numel()), "pt_train_correction")
+        return l0.value, l1.value
+
+    def apply_correction(self, v: torch.Tensor) -> torch.Tensor:
+        z = torch.empty_like(v)
+        check(lib().pt_apply_correction(self._ctx, v.shape[0], _ptr(v), _ptr(z), _ptr(self._scratch),
+                                        self._scratch.numel()), "pt_apply_correction")
+        return z
 
     def set_option(self, option: int, value: int) -> None:
         """Tuning option (PT_OPT_LAYER_GROUP: sources per CTA of the batched local solves)."""

@@ -22,9 +22,12 @@ EXPORTS = [
     "pt_layer_partition", "pt_workspace_size", "pt_create", "pt_solve", "pt_solve_host", "pt_apply_matvec",
     "pt_apply_precond", "pt_apply_D_inverse", "pt_apply_R", "pt_rhs", "pt_get_block", "pt_last_solve_stats",
     "pt_destroy", "pt_status_string", "pt_last_error", "pt_rhs_noalloc", "pt_apply", "pt_plr_stats",
-    "pt_volume_residual", "pt_set_option",
+    "pt_volume_residual", "pt_set_option", "pt_correction_nparams", "pt_set_correction", "pt_get_correction",
+    "pt_correction_scratch_bytes", "pt_correction_forward", "pt_correction_grad", "pt_train_bytes",
+    "pt_train_correction", "pt_apply_correction",
 ]
 PT_OPT_LAYER_GROUP = 1
+PT_OPT_LEARNED = 2
 
 
 class Params(C.Structure):
@@ -32,7 +35,7 @@ class Params(C.Structure):
         ("nx", C.c_int32), ("nz", C.c_int32), ("npml", C.c_int32), ("L", C.c_int32),
         ("h", C.c_double), ("omega", C.c_double), ("pml_C", C.c_double),
         ("precision", C.c_int32), ("gs_iters", C.c_int32), ("max_sources", C.c_int32), ("max_krylov", C.c_int32),
-        ("plr", C.c_int32), ("plr_eps", C.c_double), ("plr_rmax", C.c_int32),
+        ("plr", C.c_int32), ("plr_eps", C.c_double), ("plr_rmax", C.c_int32), ("learned", C.c_int32),
     ]
 
 
@@ -70,6 +73,17 @@ def lib() -> C.CDLL:
     L.pt_plr_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
     L.pt_volume_residual.argtypes = [vp, i32, vp, vp, C.POINTER(f64), vp, sz]
     L.pt_get_block.argtypes = [vp, i32, i32, i32, vp]
+    L.pt_set_option.argtypes = [vp, i32, i32]
+    i64, u64 = C.c_int64, C.c_uint64
+    L.pt_correction_nparams.argtypes = [C.POINTER(i64)]
+    L.pt_set_correction.argtypes = [vp, vp, i64]
+    L.pt_get_correction.argtypes = [vp, vp, i64]
+    L.pt_correction_scratch_bytes.argtypes = [vp, i32, C.POINTER(sz)]
+    L.pt_correction_forward.argtypes = [vp, i32, vp, vp, vp, sz]
+    L.pt_correction_grad.argtypes = [vp, i32, vp, vp, C.POINTER(f64), vp, vp, sz]
+    L.pt_train_bytes.argtypes = [vp, i32, i32, C.POINTER(sz)]
+    L.pt_train_correction.argtypes = [vp, i32, vp, vp, i32, i32, f64, u64, C.POINTER(f64), C.POINTER(f64), vp, sz]
+    L.pt_apply_correction.argtypes = [vp, i32, vp, vp, vp, sz]
     L.pt_last_solve_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
     L.pt_destroy.argtypes = [vp]
     L.pt_destroy.restype = None

@@ -5,6 +5,7 @@
 // Algorithm 2 with flexible GMRES (right preconditioned by Algorithm 4,
 // Section 4.2) driven from the host, one stream synchronisation per iteration.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -14,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <mutex>
 #include <new>
 #include <string>
@@ -62,6 +64,19 @@ cudaError_t launch_tc_apply(int, const CUtensorMap&, const CUtensorMap&, const C
                             double, int*, cudaStream_t);
 cudaError_t launch_layer_solve_batch(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
                                      const cd*, const cd*, cd*, cd*, const int*, int, int, cudaStream_t);
+cudaError_t nn_forward(const __nv_bfloat16*, const float*, const float*, long, int, float*, float*, float*,
+                       cudaStream_t);
+cudaError_t nn_backward(const __nv_bfloat16*, const float*, long, int, const float*, const float*, const float*,
+                        const float*, float*, float*, float*, float*, double*, cudaStream_t);
+cudaError_t nn_to_bf16(const float*, __nv_bfloat16*, cudaStream_t);
+cudaError_t nn_adam(float*, float*, float*, const float*, __nv_bfloat16*, double, int, cudaStream_t);
+cudaError_t nn_rms(const cd*, int, size_t, double*, cudaStream_t);
+cudaError_t nn_features(const cd*, int, int, int, int, const double*, float*, long, cudaStream_t);
+cudaError_t nn_unfeatures(const float*, int, int, int, int, const double*, cd*, bool, cudaStream_t);
+cudaError_t nn_gather(const float*, long, const int*, int, int, int, float*, cudaStream_t);
+cudaError_t nn_sub(const cd*, const cd*, cd*, size_t, cudaStream_t);
+cudaError_t nn_sumsq(const float*, long, double*, cudaStream_t);
+cudaError_t nn_scale(float*, long, float, cudaStream_t);
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
@@ -131,6 +146,9 @@ struct Plan {
   std::vector<TcKey> tk_mv, tk_R, tk_sw;
   std::vector<int> tk_sw_off, tk_sw_cnt;
   int tc_keys_max = 0;
+  // learned correction: inference buffers for nn_cs sources at a time
+  bool learned = false;
+  int nn_cs = 0;
 };
 
 pt_status make_plan(const pt_params* p, Plan& P) {
@@ -144,14 +162,20 @@ pt_status make_plan(const pt_params* p, Plan& P) {
     return fail(PT_ERR_ARG, "unknown precision");
   if (p->precision == PT_MIXED_TC && p->plr) return fail(PT_ERR_ARG, "PT_MIXED_TC applies dense blocks (plr = 0)");
   if (p->gs_iters < 1 || p->gs_iters > 16) return fail(PT_ERR_ARG, "gs_iters must be in 1..16");
+  if (p->learned != 0 && p->learned != 1) return fail(PT_ERR_ARG, "learned must be 0 or 1");
   if (p->max_sources < 1 || p->max_krylov < 1 || p->max_krylov > 512)
     return fail(PT_ERR_ARG, "max_sources >= 1 and 1 <= max_krylov <= 512");
+  P.learned = p->learned == 1;
   P.nt = p->nx + 2 * p->npml;
   P.Nz = p->nz + 2 * p->npml;
   P.L = p->L;
   P.T = 2 * (P.L - 1);
   P.T4 = 4 * (P.L - 1);
   P.N = (size_t)P.T4 * P.nt;
+  if (P.learned) {  // inference in chunks of about 64 Ki positions (at least one source)
+    const long per = (long)(P.L - 1) * P.nt;
+    P.nn_cs = (int)std::max<long>(1, std::min<long>(p->max_sources, 65536 / per));
+  }
   P.ld32 = (P.nt + 3) & ~3;
   P.g = Geometry{P.nt, P.Nz, p->npml, P.L, p->h, p->omega, p->pml_C};
   // near-equal split: the first (N_z mod L) layers get one extra row
@@ -259,6 +283,10 @@ struct Persist {
   TcKey* tck_sw;
   unsigned long long* tc_max;
   double* m_ext;        // squared slowness on the extended grid (volume residual)
+  // learned correction: FP32 master weights, BF16 copy, Adam moments, gradient, loss
+  float *nn_theta, *nn_m, *nn_v, *nn_grad;
+  __nv_bfloat16* nn_wbf;
+  double* nn_loss;
 };
 
 Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* bytes) {
@@ -318,6 +346,12 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
     q.tc_max = c.take<unsigned long long>(4);
   }
   q.m_ext = c.take<double>((size_t)P.Nz * P.nt);
+  q.nn_theta = c.take<float>(kNnParams);
+  q.nn_m = c.take<float>(kNnParams);
+  q.nn_v = c.take<float>(kNnParams);
+  q.nn_grad = c.take<float>(kNnParams);
+  q.nn_wbf = c.take<__nv_bfloat16>(kNnParams);
+  q.nn_loss = c.take<double>(4);
   if (bytes) *bytes = c.off;
   return q;
 }
@@ -351,6 +385,8 @@ struct SolveBufs {
   __half *tc_bhi, *tc_blo;  // staged tensor-core operands
   float *tc_scale, *tc_inv;
   double* vres;     // volume residual partials
+  double* nn_rms;   // learned correction: per-source RMS of the input
+  float *nn_X, *nn_A, *nn_Y;  // features, two W x P activation buffers, outputs
 };
 
 SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base, size_t* bytes) {
@@ -388,6 +424,13 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
     b.tc_inv = c.take<float>(S);
   }
   b.vres = c.take<double>((size_t)S + (size_t)S * 2 * 512);
+  if (P.learned) {
+    const size_t Pm = (size_t)P.nn_cs * (P.L - 1) * P.nt;
+    b.nn_rms = c.take<double>(S);
+    b.nn_X = c.take<float>(kNnCin * Pm);
+    b.nn_A = c.take<float>(2 * kNnW * Pm);
+    b.nn_Y = c.take<float>(kNnCin * Pm);
+  }
   if (host_staging) {
     b.fdev = c.take<cd>((size_t)S * P.Nz * P.nt);
     b.udev = c.take<cd>((size_t)S * P.Nz * P.nt);
@@ -579,6 +622,11 @@ struct pt_ctx {
   __half *tc_bhi = nullptr, *tc_blo = nullptr;
   float *tc_scale = nullptr, *tc_inv = nullptr;
   int opt_layer_group = 0;  // PT_OPT_LAYER_GROUP
+  // learned correction
+  bool nn_ready = false;    // weights set or trained
+  int nn_t = 0;             // Adam steps taken
+  int opt_learned = 0;      // PT_OPT_LEARNED
+  int learned_used = 0;     // cycles of the last solve that applied the correction
 };
 
 static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
@@ -1054,12 +1102,309 @@ extern "C" pt_status pt_volume_residual(pt_ctx* ctx, int32_t nsrc, const pt_c128
 
 extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
   if (!ctx) return fail(PT_ERR_ARG, "ctx is NULL");
+  if (option == PT_OPT_LEARNED) {
+    if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_LEARNED must be 0 or 1");
+    if (value == 1 && !ctx->P.learned) return fail(PT_ERR_ARG, "context created with learned = 0");
+    if (value == 1 && !ctx->nn_ready) return fail(PT_ERR_ARG, "no correction weights set or trained");
+    ctx->opt_learned = value;
+    return PT_OK;
+  }
   if (option == PT_OPT_LAYER_GROUP) {
     if (value != 0 && value != 8 && value != 16 && value != 32) return fail(PT_ERR_ARG, "layer group must be 0, 8, 16 or 32");
     ctx->opt_layer_group = value;
     return PT_OK;
   }
   return fail(PT_ERR_ARG, "unknown option");
+}
+
+// ---- learned correction of the preconditioner ---------------------------------
+namespace {
+
+// z (+)= N_theta(v) for S permuted residuals, nn_cs sources at a time
+cudaError_t do_correction(pt_ctx* c, int S, const cd* v, cd* z, const SolveBufs& B, bool add) {
+  const Plan& P = c->P;
+  cudaStream_t s = c->stream;
+  cudaError_t e = nn_rms(v, S, P.N, B.nn_rms, s);
+  c->launches++;
+  const long per = (long)(P.L - 1) * P.nt;
+  for (int s0 = 0; s0 < S && e == cudaSuccess; s0 += P.nn_cs) {
+    const int ns = std::min(P.nn_cs, S - s0);
+    const long Pn = ns * per;
+    e = nn_features(v, s0, ns, P.L, P.nt, B.nn_rms, B.nn_X, Pn, s);
+    if (e == cudaSuccess) e = nn_forward(c->d.nn_wbf, c->d.nn_theta, B.nn_X, Pn, P.nt, nullptr, B.nn_A, B.nn_Y, s);
+    if (e == cudaSuccess) e = nn_unfeatures(B.nn_Y, s0, ns, P.L, P.nt, B.nn_rms, z, add, s);
+    c->launches += 6;
+  }
+  return e;
+}
+
+// Training buffers for P positions: features, targets, kept pre-activations and
+// activations, outputs and their gradient, two W x P gradient buffers.
+struct NnBufs {
+  float *X, *T, *H, *A, *Y, *dY, *dA, *dH;
+};
+NnBufs carve_nn(Carver& c, long P) {
+  NnBufs b{};
+  b.X = c.take<float>((size_t)kNnCin * P);
+  b.T = c.take<float>((size_t)kNnCin * P);
+  b.H = c.take<float>((size_t)3 * kNnW * P);
+  b.A = c.take<float>((size_t)3 * kNnW * P);
+  b.Y = c.take<float>((size_t)kNnCin * P);
+  b.dY = c.take<float>((size_t)kNnCin * P);
+  b.dA = c.take<float>((size_t)kNnW * P);
+  b.dH = c.take<float>((size_t)kNnW * P);
+  return b;
+}
+
+// Seeded default weights: uniform with variance 1 / fan-in for W1..W3 (splitmix64
+// stream), zero last layer and biases, so the initial correction is zero.
+void nn_default_init(std::vector<float>& th, uint64_t seed) {
+  uint64_t st = seed;
+  auto next = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  th.assign(kNnParams, 0.f);
+  auto fill = [&](size_t off, size_t n, double fan_in) {
+    const double a = std::sqrt(3.0 / fan_in);
+    for (size_t q = 0; q < n; ++q) th[off + q] = (float)((2.0 * ((double)(next() >> 11) * 0x1.0p-53) - 1.0) * a);
+  };
+  fill(kNnOffW1, (size_t)kNnW * kNnCin * kNnK1, kNnCin * kNnK1);
+  fill(kNnOffW2, (size_t)kNnW * kNnW, kNnW);
+  fill(kNnOffW3, (size_t)kNnW * kNnW, kNnW);
+}
+
+pt_status nn_upload(pt_ctx* c, const float* host) {
+  cudaStream_t s = c->stream;
+  PT_CUDA(cudaMemcpyAsync(c->d.nn_theta, host, kNnParams * sizeof(float), cudaMemcpyHostToDevice, s));
+  PT_CUDA(cudaMemsetAsync(c->d.nn_m, 0, kNnParams * sizeof(float), s));
+  PT_CUDA(cudaMemsetAsync(c->d.nn_v, 0, kNnParams * sizeof(float), s));
+  PT_CUDA(nn_to_bf16(c->d.nn_theta, c->d.nn_wbf, s));
+  PT_CUDA(cudaStreamSynchronize(s));
+  c->nn_t = 0;
+  c->nn_ready = true;
+  return PT_OK;
+}
+
+}  // namespace
+
+extern "C" pt_status pt_correction_nparams(int64_t* nparams) {
+  if (!nparams) return fail(PT_ERR_ARG, "nparams is NULL");
+  *nparams = (int64_t)kNnParams;
+  return PT_OK;
+}
+
+extern "C" pt_status pt_set_correction(pt_ctx* ctx, const float* params, int64_t nparams) {
+  if (!ctx || !params) return fail(PT_ERR_ARG, "bad arguments");
+  if (nparams != (int64_t)kNnParams) return fail(PT_ERR_ARG, "nparams does not match the network");
+  return nn_upload(ctx, params);
+}
+
+extern "C" pt_status pt_get_correction(const pt_ctx* ctx, float* params, int64_t nparams) {
+  if (!ctx || !params) return fail(PT_ERR_ARG, "bad arguments");
+  if (nparams != (int64_t)kNnParams) return fail(PT_ERR_ARG, "nparams does not match the network");
+  if (!ctx->nn_ready) return fail(PT_ERR_ARG, "no correction weights set or trained");
+  PT_CUDA(cudaMemcpyAsync(params, ctx->d.nn_theta, kNnParams * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_correction_scratch_bytes(const pt_ctx* ctx, int32_t nseq, size_t* bytes) {
+  if (!ctx || !bytes || nseq < 1) return fail(PT_ERR_ARG, "bad arguments");
+  Carver c(nullptr);
+  carve_nn(c, (long)nseq * ctx->P.nt);
+  *bytes = c.off;
+  return PT_OK;
+}
+
+extern "C" pt_status pt_correction_forward(pt_ctx* ctx, int32_t nseq, const float* x, float* y, void* scratch,
+                                           size_t scratch_bytes) {
+  if (!ctx || !x || !y || !scratch || nseq < 1) return fail(PT_ERR_ARG, "bad arguments");
+  if (!ctx->nn_ready) return fail(PT_ERR_ARG, "no correction weights set or trained");
+  size_t need = 0;
+  pt_correction_scratch_bytes(ctx, nseq, &need);
+  if (scratch_bytes < need) return fail(PT_ERR_WORKSPACE, "scratch too small");
+  Carver c(scratch);
+  const long P = (long)nseq * ctx->P.nt;
+  NnBufs b = carve_nn(c, P);
+  PT_CUDA(nn_forward(ctx->d.nn_wbf, ctx->d.nn_theta, x, P, ctx->P.nt, nullptr, b.A, y, ctx->stream));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
+}
+
+extern "C" pt_status pt_correction_grad(pt_ctx* ctx, int32_t nseq, const float* x, const float* t, double* loss,
+                                        float* grad, void* scratch, size_t scratch_bytes) {
+  if (!ctx || !x || !t || !grad || !scratch || nseq < 1) return fail(PT_ERR_ARG, "bad arguments");
+  if (!ctx->nn_ready) return fail(PT_ERR_ARG, "no correction weights set or trained");
+  size_t need = 0;
+  pt_correction_scratch_bytes(ctx, nseq, &need);
+  if (scratch_bytes < need) return fail(PT_ERR_WORKSPACE, "scratch too small");
+  Carver c(scratch);
+  const long P = (long)nseq * ctx->P.nt;
+  NnBufs b = carve_nn(c, P);
+  cudaStream_t s = ctx->stream;
+  PT_CUDA(cudaMemsetAsync(grad, 0, kNnParams * sizeof(float), s));
+  PT_CUDA(cudaMemsetAsync(ctx->d.nn_loss, 0, sizeof(double), s));
+  PT_CUDA(nn_forward(ctx->d.nn_wbf, ctx->d.nn_theta, x, P, ctx->P.nt, b.H, b.A, b.Y, s));
+  PT_CUDA(nn_backward(ctx->d.nn_wbf, x, P, ctx->P.nt, b.H, b.A, b.Y, t, b.dY, b.dA, b.dH, grad, ctx->d.nn_loss, s));
+  double l = 0.0;
+  PT_CUDA(cudaMemcpyAsync(&l, ctx->d.nn_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(cudaStreamSynchronize(s));
+  if (loss) *loss = l;
+  return PT_OK;
+}
+
+namespace {
+struct TrainBufs {
+  void* solve;  // solve scratch (K^{-1} of the targets)
+  float *Xall, *Tall;
+  double* rms;
+  int* idx;
+  NnBufs nb;
+};
+TrainBufs carve_train(const pt_ctx* ctx, int npairs, int batch, void* base, size_t* bytes) {
+  const Plan& P = ctx->P;
+  size_t sb = 0;
+  carve_solve(P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &sb);
+  Carver c(base);
+  TrainBufs t{};
+  t.solve = c.take<unsigned char>(sb);
+  const long per = (long)(P.L - 1) * P.nt;
+  t.Xall = c.take<float>((size_t)kNnCin * npairs * per);
+  t.Tall = c.take<float>((size_t)kNnCin * npairs * per);
+  t.rms = c.take<double>(npairs);
+  t.idx = c.take<int>(batch);
+  t.nb = carve_nn(c, (long)batch * per);
+  if (bytes) *bytes = c.off;
+  return t;
+}
+}  // namespace
+
+extern "C" pt_status pt_train_bytes(const pt_ctx* ctx, int32_t npairs, int32_t batch, size_t* bytes) {
+  if (!ctx || !bytes || npairs < 1 || batch < 1 || batch > npairs) return fail(PT_ERR_ARG, "bad arguments");
+  carve_train(ctx, npairs, batch, nullptr, bytes);
+  return PT_OK;
+}
+
+extern "C" pt_status pt_train_correction(pt_ctx* ctx, int32_t npairs, const pt_c128* r, const pt_c128* e,
+                                         int32_t steps, int32_t batch, double lr, uint64_t seed, double* loss_first,
+                                         double* loss_last, void* scratch, size_t scratch_bytes) {
+  if (!ctx || !r || !e || !scratch || npairs < 1 || batch < 1 || batch > npairs || steps < 0 || !(lr > 0))
+    return fail(PT_ERR_ARG, "bad arguments");
+  if ((uintptr_t)scratch % kAlign) return fail(PT_ERR_ARG, "scratch must be 256-byte aligned");
+  size_t need = 0;
+  carve_train(ctx, npairs, batch, nullptr, &need);
+  if (scratch_bytes < need) return fail(PT_ERR_WORKSPACE, "scratch too small");
+  TrainBufs tb = carve_train(ctx, npairs, batch, scratch, nullptr);
+  const Plan& P = ctx->P;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->nn_ready) {
+    std::vector<float> th;
+    nn_default_init(th, seed);
+    pt_status st = nn_upload(ctx, th.data());
+    if (st != PT_OK) return st;
+  }
+  // targets (e - K^{-1} r) / RMS(r) and inputs P r / RMS(r) as features, max_sources pairs at a time
+  SolveBufs B = carve_solve(P, ctx->prm.max_sources, ctx->prm.max_krylov, false, tb.solve, nullptr);
+  const long per = (long)(P.L - 1) * P.nt;
+  const long Pall = (long)npairs * per;
+  const cd* rd = reinterpret_cast<const cd*>(r);
+  const cd* ed = reinterpret_cast<const cd*>(e);
+  for (int p0 = 0; p0 < npairs; p0 += ctx->prm.max_sources) {
+    const int ns = std::min(ctx->prm.max_sources, npairs - p0);
+    {
+      pt_status bs = bind_call(ctx, B, ns);
+      if (bs != PT_OK) return bs;
+    }
+    const cd* rp = rd + (size_t)p0 * P.N;
+    PT_CUDA(do_precond(ctx, ns, rp, B.x, B.t, B.u1));
+    PT_CUDA(nn_sub(ed + (size_t)p0 * P.N, B.x, B.w, (size_t)ns * P.N, s));
+    PT_CUDA(nn_rms(rp, ns, P.N, tb.rms + p0, s));
+    PT_CUDA(nn_features(rp, 0, ns, P.L, P.nt, tb.rms + p0, tb.Xall + (size_t)p0 * per, Pall, s));
+    PT_CUDA(nn_features(B.w, 0, ns, P.L, P.nt, tb.rms + p0, tb.Tall + (size_t)p0 * per, Pall, s));
+  }
+  // Train on targets scaled to unit RMS (tau = 1 / RMS): the last layer is linear, so
+  // W4 and b4 are multiplied by tau before and divided by it after, and the
+  // stored network keeps predicting the unscaled defect.  Adam restarts per call.
+  double tau = 1.0;
+  {
+    PT_CUDA(cudaMemsetAsync(ctx->d.nn_loss + 1, 0, sizeof(double), s));
+    PT_CUDA(nn_sumsq(tb.Tall, (long)kNnCin * Pall, ctx->d.nn_loss + 1, s));
+    double ss = 0.0;
+    PT_CUDA(cudaMemcpyAsync(&ss, ctx->d.nn_loss + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    const double rmsT = std::sqrt(ss / ((double)kNnCin * Pall));
+    if (rmsT > 0.0 && std::isfinite(rmsT)) tau = 1.0 / rmsT;
+  }
+  PT_CUDA(nn_scale(tb.Tall, (long)kNnCin * Pall, (float)tau, s));
+  PT_CUDA(nn_scale(ctx->d.nn_theta + kNnOffW4, (long)(kNnParams - kNnOffW4), (float)tau, s));
+  PT_CUDA(cudaMemsetAsync(ctx->d.nn_m, 0, kNnParams * sizeof(float), s));
+  PT_CUDA(cudaMemsetAsync(ctx->d.nn_v, 0, kNnParams * sizeof(float), s));
+  PT_CUDA(nn_to_bf16(ctx->d.nn_theta, ctx->d.nn_wbf, s));
+  ctx->nn_t = 0;
+  // Adam on minibatches drawn without replacement within each pass over the pairs
+  std::vector<int> order(npairs), pick(batch);
+  for (int q = 0; q < npairs; ++q) order[q] = q;
+  uint64_t st = seed ^ 0x5DEECE66Dull;
+  auto next = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto shuffle = [&]() {
+    for (int q = npairs - 1; q > 0; --q) std::swap(order[q], order[next() % (uint64_t)(q + 1)]);
+  };
+  shuffle();
+  int cursor = 0;
+  const long Pb = (long)batch * per;
+  for (int it = 0; it < steps; ++it) {
+    for (int q = 0; q < batch; ++q) {
+      if (cursor == npairs) { shuffle(); cursor = 0; }
+      pick[q] = order[cursor++];
+    }
+    PT_CUDA(cudaMemcpyAsync(tb.idx, pick.data(), batch * sizeof(int), cudaMemcpyHostToDevice, s));
+    PT_CUDA(nn_gather(tb.Xall, Pall, tb.idx, batch, P.L - 1, P.nt, tb.nb.X, s));
+    PT_CUDA(nn_gather(tb.Tall, Pall, tb.idx, batch, P.L - 1, P.nt, tb.nb.T, s));
+    PT_CUDA(cudaMemsetAsync(ctx->d.nn_grad, 0, kNnParams * sizeof(float), s));
+    PT_CUDA(cudaMemsetAsync(ctx->d.nn_loss, 0, sizeof(double), s));
+    PT_CUDA(nn_forward(ctx->d.nn_wbf, ctx->d.nn_theta, tb.nb.X, Pb, P.nt, tb.nb.H, tb.nb.A, tb.nb.Y, s));
+    PT_CUDA(nn_backward(ctx->d.nn_wbf, tb.nb.X, Pb, P.nt, tb.nb.H, tb.nb.A, tb.nb.Y, tb.nb.T, tb.nb.dY, tb.nb.dA,
+                        tb.nb.dH, ctx->d.nn_grad, ctx->d.nn_loss, s));
+    PT_CUDA(nn_adam(ctx->d.nn_theta, ctx->d.nn_m, ctx->d.nn_v, ctx->d.nn_grad, ctx->d.nn_wbf, lr, ++ctx->nn_t, s));
+    if (it == 0 || it == steps - 1) {
+      double l = 0.0;
+      PT_CUDA(cudaMemcpyAsync(&l, ctx->d.nn_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+      PT_CUDA(cudaStreamSynchronize(s));
+      // losses are reported in the unscaled units of the defect
+      if (it == 0 && loss_first) *loss_first = l / (tau * tau);
+      if (it == steps - 1 && loss_last) *loss_last = l / (tau * tau);
+    }
+  }
+  PT_CUDA(nn_scale(ctx->d.nn_theta + kNnOffW4, (long)(kNnParams - kNnOffW4), (float)(1.0 / tau), s));
+  PT_CUDA(nn_to_bf16(ctx->d.nn_theta, ctx->d.nn_wbf, s));
+  PT_CUDA(cudaStreamSynchronize(s));
+  pt_status stt = read_status(ctx);
+  return stt;
+}
+
+extern "C" pt_status pt_apply_correction(pt_ctx* ctx, int32_t nsrc, const pt_c128* v, pt_c128* z, void* scratch,
+                                         size_t scratch_bytes) {
+  if (!ctx || !v || !z) return fail(PT_ERR_ARG, "bad arguments");
+  if (!ctx->P.learned) return fail(PT_ERR_ARG, "context created with learned = 0");
+  if (!ctx->nn_ready) return fail(PT_ERR_ARG, "no correction weights set or trained");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  PT_CUDA(do_correction(ctx, nsrc, reinterpret_cast<const cd*>(v), reinterpret_cast<cd*>(z), B, false));
+  PT_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PT_OK;
 }
 
 extern "C" pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leaves) {
@@ -1165,6 +1510,10 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
   bool first = true;
   int used = 0;
   std::vector<double> nrm(S);
+  // learned correction: on while every cycle that used it at least halved the true residual
+  bool learned_on = c->opt_learned && c->nn_ready && P.learned;
+  std::vector<double> rel_prev(S, 1.0);
+  c->learned_used = 0;
   while (true) {
     // V_0 = r / ||r||, g = (||r||, 0, ...), H = 0
     PT_CUDA(cudaMemsetAsync(B.H, 0, (size_t)S * (m + 1) * m * sizeof(cd), s));
@@ -1192,6 +1541,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
       cd* Vj = B.V + (size_t)j * S * N;
       cd* Zj = B.Z + (size_t)j * S * N;
       PT_CUDA(do_precond(c, S, Vj, Zj, B.t, B.u1));
+      if (learned_on) PT_CUDA(do_correction(c, S, Vj, Zj, B, /*add=*/true));
       PT_CUDA(do_matvec(c, S, Zj, B.w, /*exact=*/false));
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         c->launches += 3;
@@ -1230,11 +1580,18 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     PT_CUDA(cudaMemcpyAsync(nrm.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
     PT_CUDA(cudaStreamSynchronize(s));
     bool all = true;
+    bool poor = false;
     for (int q = 0; q < S; ++q) {
       if (done[q]) continue;
       rel[q] = nrm[q] / beta[q];
+      if (!(rel[q] <= 0.5 * rel_prev[q])) poor = true;
+      rel_prev[q] = rel[q];
       if (rel[q] <= tol) done[q] = 1;
       else all = false;
+    }
+    if (learned_on) {
+      c->learned_used++;
+      if (poor) learned_on = false;  // fall back to the plain preconditioner
     }
     if (all || used >= max_it) break;
   }

@@ -22,6 +22,19 @@ typedef float2 cf;
 constexpr int kMaxLayers = 256;
 constexpr int kMaxNloc = 118;  // Gauss-Jordan of one Schur complement held in 227 KB of shared memory
 
+// Learned correction network (flat parameter layout shared with the oracle):
+// W1 (W, 8, 7) | b1 (W) | W2 (W, W) | b2 (W) | W3 (W, W) | b3 (W) | W4 (8, W) | b4 (8)
+constexpr int kNnCin = 8, kNnK1 = 7, kNnW = 256;
+constexpr size_t kNnOffW1 = 0;
+constexpr size_t kNnOffB1 = kNnOffW1 + (size_t)kNnW * kNnCin * kNnK1;
+constexpr size_t kNnOffW2 = kNnOffB1 + kNnW;
+constexpr size_t kNnOffB2 = kNnOffW2 + (size_t)kNnW * kNnW;
+constexpr size_t kNnOffW3 = kNnOffB2 + kNnW;
+constexpr size_t kNnOffB3 = kNnOffW3 + (size_t)kNnW * kNnW;
+constexpr size_t kNnOffW4 = kNnOffB3 + kNnW;
+constexpr size_t kNnOffB4 = kNnOffW4 + (size_t)kNnCin * kNnW;
+constexpr size_t kNnParams = kNnOffB4 + kNnCin;
+
 // Device error word bits (ctx->status on the device)
 constexpr int kErrSingular = 1;
 constexpr int kErrNumeric = 2;
