@@ -171,6 +171,98 @@ def cpu_baseline(wl: W.Workload, sample_solves: int, c: np.ndarray, omega: float
                       f"{wl.name} problem (factorization {t_fact:.1f} s excluded; SciPy SuperLU is single-threaded)"}
 
 
+def batched_section(args, dev, pg, pk):
+    """The batched form on the layered 1023 x 2047 workload (L = 32, 256 sources along the
+    top row): tensor-core block products (PT_MIXED_TC), source-batched FP32 local solves,
+    FP64 flexible GMRES with double-float restarts; against the plain FP64 form solving
+    the same sources one at a time."""
+    import torch
+
+    from paper_1410_5910_gb300 import PT_FP64, PT_MIXED_TC, PolarTrace, default_pml_strength
+
+    wl = W.LAYERED_1023x2047
+    S = args.batched_sources
+    c = wl.c_ext()
+    om = wl.omega(c)
+    pmlC = default_pml_strength(float(c.max()))
+    c_dev = torch.from_numpy(c).to(dev)
+    f = torch.from_numpy(sources_for(wl, S)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    tc = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, om, c_dev, pml_C=pmlC, precision=PT_MIXED_TC, max_sources=S,
+                    max_krylov=40)
+    torch.cuda.synchronize(dev)
+    t_off = time.perf_counter() - t0
+    u = torch.empty_like(f)
+    for _ in range(args.warmup):
+        _, _, its, rel = tc.solve(f, tol=wl.tol, u=u, want_traces=False)
+    steps = max(2, args.batched_steps)
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            _, _, its, rel = tc.solve(f, tol=wl.tol, u=u, want_traces=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(pg)
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / steps)
+    cycles, _ = tc.last_solve_cycles()
+    launches, _ = tc.last_solve_stats()
+    vres = tc.volume_residual(f, u)
+    # tensor-pipe roofline of the three-pass matvec: executed MMA flops / time
+    x = torch.randn((S, tc.T4, tc.nt), dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        tc.apply("matvec", x, working=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a_, b_ in ev:
+        a_.record(stream)
+        tc.apply("matvec", x, working=True)
+        b_.record(stream)
+    torch.cuda.synchronize(dev)
+    t_mv = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
+    nblocks = 16 * (wl.L - 2) + 8
+    cplx_flops = 8.0 * nblocks * wl.nt * wl.nt * S
+    peak = pk.get("bf16_tflops")  # a kernel timed alone: the burst figure
+    roof_tc = {"kernel": "tc_apply_kernel (tcgen05 FP16 x FP16 -> FP32, three hi/lo passes)", "bound": "tensor",
+               "achieved": 3 * cplx_flops / t_mv / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": None,
+               "traffic": None, "complex_tflops": cplx_flops / t_mv / 1e12, "launch_ms": t_mv * 1e3,
+               "peak_source": "measured bf16 dense burst (FP16 runs at the same rate)"}
+    roof_tc["frac"] = roof_tc["achieved"] / roof_tc["peak"] if peak else None
+    del tc, x, u
+    torch.cuda.empty_cache()
+    out = {"workload": wl.name, "sources_per_step": S, "tol": wl.tol, "value": S / (ms / 1e3),
+           "unit": "solves/s", "ms_per_step": ms, "steps": steps, "gmres_iterations_max": max(its),
+           "gmres_iterations_min": min(its), "restart_cycles": cycles, "true_relres_max": max(rel),
+           "volume_residual_max": max(vres), "offline_s": t_off, "gpu_launches_per_step": launches,
+           "clocks": clk.summary(), "roofline_tc_matvec": roof_tc,
+           "form": "tensor-core block products (FP16 hi/lo, FP32 accumulation), FP32 source-batched local "
+                   "solves, FP64 flexible GMRES with double-float restarts"}
+    if not args.no_plain:
+        t0 = time.perf_counter()
+        p64 = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, om, c_dev, pml_C=pmlC, precision=PT_FP64,
+                         max_sources=1, max_krylov=40)
+        torch.cuda.synchronize(dev)
+        t_off64 = time.perf_counter() - t0
+        f1 = f[:1].contiguous()
+        u1 = torch.empty_like(f1)
+        for _ in range(2):
+            p64.solve(f1, tol=wl.tol, u=u1, want_traces=False)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(3):
+            _, _, its64, _ = p64.solve(f1, tol=wl.tol, u=u1, want_traces=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / 3
+        out["plain_fp64"] = {"value": 1e3 / ms64, "unit": "solves/s", "ms_per_solve": ms64,
+                             "gmres_iterations": its64, "offline_s": t_off64, "sources_per_solve": 1}
+        del p64
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, wl, rank, world, pg):
     """--impl reference: the CPU oracle timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -219,6 +311,9 @@ def main():
     ap.add_argument("--no-plr", action="store_true", help="skip the partitioned low-rank variants")
     ap.add_argument("--plr-eps", type=float, default=1e-9)
     ap.add_argument("--plr-rmax", type=int, default=24)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core form (256 sources)")
+    ap.add_argument("--batched-sources", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -343,6 +438,12 @@ def main():
     e2e = {"value": total_solves * args.steps / dt, "unit": "solves/s",
            "h2d_bytes_per_step": int(f_pin.numel() * 16), "d2h_bytes_per_step": int(u_pin.numel() * 16)}
 
+    batched = None
+    if not args.no_batched:
+        del solver, fp64_solver, scratch
+        torch.cuda.empty_cache()
+        batched = batched_section(args, dev, pg, pk)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_sample, c, om)
@@ -365,6 +466,8 @@ def main():
         }
         if plain is not None:
             line["plain_fp64"] = plain
+        if batched is not None:
+            line["batched"] = batched
         line.update(plr_results)
         line.update(extra)
         print(json.dumps(line), flush=True)

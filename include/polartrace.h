@@ -295,6 +295,10 @@ pt_status pt_get_block(pt_ctx* ctx, int32_t layer, int32_t j, int32_t k, pt_c128
  * the GMRES iteration count of the slowest source. */
 pt_status pt_last_solve_stats(const pt_ctx* ctx, int64_t* kernel_launches, int32_t* max_iterations);
 
+/* Restart cycles of the last pt_solve (each ends with an explicit residual) and
+ * how many of them applied the learned correction (host outputs, NULL allowed). */
+pt_status pt_last_solve_cycles(const pt_ctx* ctx, int32_t* cycles, int32_t* learned_cycles);
+
 void pt_destroy(pt_ctx* ctx);
 const char* pt_status_string(pt_status s);
 /* Text of the last error recorded on this thread (empty when none). */

@@ -142,6 +142,12 @@ class PolarTrace:
         check(lib().pt_last_solve_stats(self._ctx, C.byref(n), C.byref(m)), "pt_last_solve_stats")
         return n.value, m.value
 
+    def last_solve_cycles(self):
+        """(restart cycles, cycles that applied the learned correction) of the last solve."""
+        a, b = C.c_int32(), C.c_int32()
+        check(lib().pt_last_solve_cycles(self._ctx, C.byref(a), C.byref(b)), "pt_last_solve_cycles")
+        return a.value, b.value
+
     # ---- building blocks (testing) -----------------------------------------
     def _vec(self, S):
         return torch.empty((S, self.T4, self.nt), dtype=torch.complex128, device=self.device)

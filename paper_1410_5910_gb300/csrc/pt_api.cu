@@ -627,6 +627,7 @@ struct pt_ctx {
   int nn_t = 0;             // Adam steps taken
   int opt_learned = 0;      // PT_OPT_LEARNED
   int learned_used = 0;     // cycles of the last solve that applied the correction
+  int last_cycles = 0;      // restart cycles (explicit residuals) of the last solve
 };
 
 static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
@@ -1191,6 +1192,13 @@ pt_status nn_upload(pt_ctx* c, const float* host) {
 
 }  // namespace
 
+extern "C" pt_status pt_last_solve_cycles(const pt_ctx* ctx, int32_t* cycles, int32_t* learned_cycles) {
+  if (!ctx) return fail(PT_ERR_ARG, "ctx is NULL");
+  if (cycles) *cycles = ctx->last_cycles;
+  if (learned_cycles) *learned_cycles = ctx->learned_used;
+  return PT_OK;
+}
+
 extern "C" pt_status pt_correction_nparams(int64_t* nparams) {
   if (!nparams) return fail(PT_ERR_ARG, "nparams is NULL");
   *nparams = (int64_t)kNnParams;
@@ -1514,6 +1522,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
   bool learned_on = c->opt_learned && c->nn_ready && P.learned;
   std::vector<double> rel_prev(S, 1.0);
   c->learned_used = 0;
+  c->last_cycles = 0;
   while (true) {
     // V_0 = r / ||r||, g = (||r||, 0, ...), H = 0
     PT_CUDA(cudaMemsetAsync(B.H, 0, (size_t)S * (m + 1) * m * sizeof(cd), s));
@@ -1531,11 +1540,21 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     }
     std::vector<int> active(S, 0);
     int nact = 0;
+    // Cycle target: tol ||P b||.  In PT_MIXED_TC the tensor-core matvec (~1e-5 relative)
+    // lets the true residual stall near 1e-4 of the cycle's starting residual: a cycle
+    // that cannot reach tol stops 3e-4 below its start (further iterations would be
+    // lost until the double-float restart); one that can aims at 0.3 tol, so that the
+    // true residual, its estimate plus that floor, lands under tol without another
+    // restart.
+    std::vector<double> target(S);
     for (int q = 0; q < S; ++q) {
       kk[q] = 0;
       if (!done[q]) { active[q] = 1; nact++; }
+      target[q] = tol * beta[q];
+      if (tcmode(c)) target[q] = 3e-4 * nrm[q] > tol * beta[q] ? 3e-4 * nrm[q] : 0.3 * tol * beta[q];
     }
     if (nact == 0 || used >= max_it) break;
+    c->last_cycles++;
     int j = 0;
     for (; j < m && used < max_it; ++j) {
       cd* Vj = B.V + (size_t)j * S * N;
@@ -1557,7 +1576,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
       bool all = true;
       for (int q = 0; q < S; ++q) {
         if (!active[q] || kk[q]) continue;
-        if (!(c->resid_h[q] > tol * beta[q])) kk[q] = j + 1;  // converged (or NaN: stop it too)
+        if (!(c->resid_h[q] > target[q])) kk[q] = j + 1;  // cycle done (or NaN: stop it too)
         else all = false;
       }
       if (all) { ++j; break; }

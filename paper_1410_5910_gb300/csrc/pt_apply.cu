@@ -16,7 +16,8 @@
 //         high parts (FMA), error-free two-sum accumulation, cross terms in a
 //         compensation word.  About 2^-45 relative accuracy, FP32 pipes, HBM bound.
 // A CTA computes rows_per_cta consecutive rows of one output trace for one
-// source; inputs are staged in shared memory once per CTA.
+// source; inputs are staged in shared memory once per CTA.  The grid runs the
+// sources fastest so that a batch of sources shares each block row through L2.
 #include "pt_common.cuh"
 
 namespace pt {
@@ -57,9 +58,9 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
                                                     double alpha, double beta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ApplyRow row;
-  if (threadIdx.x == 0) row = table[blockIdx.y];
+  if (threadIdx.x == 0) row = table[blockIdx.z];
   __syncthreads();
-  const int s = blockIdx.z;
+  const int s = blockIdx.x;
   const size_t vs = (size_t)T4 * nt;
   const cd* xs = x + s * vs;
   const cd* as = aux ? aux + s * vs : nullptr;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
   __syncthreads();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r0 = blockIdx.x * rows_per_cta;
+  const int r0 = blockIdx.y * rows_per_cta;
   for (int rr = warp; rr < rows_per_cta; rr += 8) {
     const int r = r0 + rr;
     if (r >= nt) break;
@@ -156,7 +157,10 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
       val = make_double2(acc.x, acc.y);
     } else {
       const float4* xin = reinterpret_cast<const float4*>(smem_raw);  // (re_hi, im_hi, re_lo, im_lo)
+      // two independent accumulator sets (even / odd column pairs of a lane) halve the
+      // dependent two-sum chains; they are merged error-free at the end
       float Sr = 0.f, Cr = 0.f, Si = 0.f, Ci = 0.f;
+      float Sr2 = 0.f, Cr2 = 0.f, Si2 = 0.f, Ci2 = 0.f;
       const int np = ld >> 1;
       for (int t = 0; t < nterms; ++t) {
         const size_t off = (size_t)row.t[t].block * bsz + (size_t)r * ld;
@@ -165,21 +169,25 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
         const float4* xv = xin + t * ld;
         int k = lane;
         for (; k + 32 < np; k += 64) {
-          float4 h0 = __ldg(H + k), l0 = __ldg(Lo + k), h1 = __ldg(H + k + 32), l1 = __ldg(Lo + k + 32);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float4 h = u ? h1 : h0, l = u ? l1 : l0;
-            const int kk = k + 32 * u;
-            const float4 x0 = xv[2 * kk], x1 = xv[2 * kk + 1];
-            df_mac(h.x, l.x, x0.x, x0.z, Sr, Cr);
-            df_mac(-h.y, -l.y, x0.y, x0.w, Sr, Cr);
-            df_mac(h.x, l.x, x0.y, x0.w, Si, Ci);
-            df_mac(h.y, l.y, x0.x, x0.z, Si, Ci);
-            df_mac(h.z, l.z, x1.x, x1.z, Sr, Cr);
-            df_mac(-h.w, -l.w, x1.y, x1.w, Sr, Cr);
-            df_mac(h.z, l.z, x1.y, x1.w, Si, Ci);
-            df_mac(h.w, l.w, x1.x, x1.z, Si, Ci);
-          }
+          const float4 h0 = __ldg(H + k), l0 = __ldg(Lo + k), h1 = __ldg(H + k + 32), l1 = __ldg(Lo + k + 32);
+          const float4 a0 = xv[2 * k], a1 = xv[2 * k + 1];
+          const float4 b0 = xv[2 * (k + 32)], b1 = xv[2 * (k + 32) + 1];
+          df_mac(h0.x, l0.x, a0.x, a0.z, Sr, Cr);
+          df_mac(h1.x, l1.x, b0.x, b0.z, Sr2, Cr2);
+          df_mac(h0.x, l0.x, a0.y, a0.w, Si, Ci);
+          df_mac(h1.x, l1.x, b0.y, b0.w, Si2, Ci2);
+          df_mac(-h0.y, -l0.y, a0.y, a0.w, Sr, Cr);
+          df_mac(-h1.y, -l1.y, b0.y, b0.w, Sr2, Cr2);
+          df_mac(h0.y, l0.y, a0.x, a0.z, Si, Ci);
+          df_mac(h1.y, l1.y, b0.x, b0.z, Si2, Ci2);
+          df_mac(h0.z, l0.z, a1.x, a1.z, Sr, Cr);
+          df_mac(h1.z, l1.z, b1.x, b1.z, Sr2, Cr2);
+          df_mac(h0.z, l0.z, a1.y, a1.w, Si, Ci);
+          df_mac(h1.z, l1.z, b1.y, b1.w, Si2, Ci2);
+          df_mac(-h0.w, -l0.w, a1.y, a1.w, Sr, Cr);
+          df_mac(-h1.w, -l1.w, b1.y, b1.w, Sr2, Cr2);
+          df_mac(h0.w, l0.w, a1.x, a1.z, Si, Ci);
+          df_mac(h1.w, l1.w, b1.x, b1.z, Si2, Ci2);
         }
         for (; k < np; k += 32) {
           const float4 h = __ldg(H + k), l = __ldg(Lo + k);
@@ -193,6 +201,15 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
           df_mac(h.z, l.z, x1.y, x1.w, Si, Ci);
           df_mac(h.w, l.w, x1.x, x1.z, Si, Ci);
         }
+      }
+      {  // merge the second set: (S, C) += (S2, C2)
+        float s1, e1;
+        two_sum(Sr, Sr2, s1, e1);
+        Sr = s1;
+        Cr = Cr + Cr2 + e1;
+        two_sum(Si, Si2, s1, e1);
+        Si = s1;
+        Ci = Ci + Ci2 + e1;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -237,7 +254,9 @@ cudaError_t launch_apply_mode(int mode, int nt, int ld, int T4, const ApplyRow* 
                               int nsrc, int rows_per_cta, double alpha, double beta, cudaStream_t s) {
   const int elem = mode == kFP32 ? 8 : 16;
   size_t smem = 4ull * ld * elem;
-  dim3 grid((nt + rows_per_cta - 1) / rows_per_cta, nrows, nsrc);
+  // sources fastest: the CTAs that read the same block rows for different sources
+  // run together, so a batch streams each block from HBM about once (L2 reuse)
+  dim3 grid(nsrc, (nt + rows_per_cta - 1) / rows_per_cta, nrows);
   cudaError_t e = cudaSuccess;
   if (mode == kFP64) {
     e = cudaFuncSetAttribute(apply_kernel<kFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
