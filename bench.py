@@ -302,7 +302,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=W.GRF_511x1023.name, choices=sorted(W.WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "tc"])
     ap.add_argument("--sources", type=int, default=1, help="sources per step (batch)")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--cpu-sample", type=int, default=20, help="oracle back-substitutions in cpu_baseline")
@@ -326,7 +326,7 @@ def main():
 
     import torch
 
-    from paper_1410_5910_gb300 import PT_FP64, PT_MIXED_FP32, PolarTrace, default_pml_strength
+    from paper_1410_5910_gb300 import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PolarTrace, default_pml_strength
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -365,7 +365,7 @@ def main():
         ms = e0.elapsed_time(e1)
         return ms / steps, its, rel, u, clk.summary()
 
-    chosen_prec = PT_MIXED_FP32 if args.precision == "mixed" else PT_FP64
+    chosen_prec = {"fp64": PT_FP64, "mixed": PT_MIXED_FP32, "tc": PT_MIXED_TC}[args.precision]
     solver, t_off = make(chosen_prec)
     ms_local, its, rel, u, clocks = time_solves(solver, args.steps, args.warmup)
     launches, _ = solver.last_solve_stats()
@@ -452,11 +452,15 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if chosen_prec == PT_FP64 else "f64+f32",
+            "vs_baseline": None,
+            "dtype": {PT_FP64: "f64", PT_MIXED_FP32: "f64+f32", PT_MIXED_TC: "f64+f32+f16"}[chosen_prec],
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": wl.nx, "nz": wl.nz, "npml": wl.npml, "L": wl.L,
                        "medium": wl.medium, "omega": om, "sources_per_step": S, "tol": tol,
-                       "form": "mixed FP32 preconditioner, FP64 FGMRES" if chosen_prec else "plain FP64",
+                       "form": {PT_FP64: "plain FP64", PT_MIXED_FP32: "mixed: FP32 preconditioner, double-float "
+                                "matvec and local solves, FP64 FGMRES",
+                                PT_MIXED_TC: "tensor-core block products, FP32 batched local solves, FP64 "
+                                "FGMRES with double-float restarts"}[chosen_prec],
                        "blocks": "dense", "parallelism": f"replicas x{world}",
                        "l2": f"interface blocks {16 * L_ * nt * nt * 16 / 1e9:.2f} GB stream from HBM each "
                              "iteration (> 129 MB L2); no flush needed"},

@@ -64,9 +64,12 @@ typedef enum {
 typedef enum {
   PT_FP64 = 0,       /* every block product in FP64                                  */
   PT_MIXED_FP32 = 1, /* preconditioner (Algorithm 4) applies FP32 copies of the
-                        blocks; the GMRES matvec and the local solves run in
-                        double-float (FP32 pairs, ~1e-14); Arnoldi, least squares
-                        and the explicit residual in FP64 (flexible GMRES)          */
+                        blocks; the GMRES matvec runs in double-float (FP32 pairs,
+                        ~1e-14); local solves (right-hand side, reconstruction) in
+                        FP32 with the FP64 factors rounded to complex64 (~1e-6 on
+                        the field; PT_OPT_LOCAL_SOLVE = 1 selects double-float);
+                        Arnoldi, least squares and the explicit residual in FP64
+                        (flexible GMRES)                                            */
   PT_MIXED_TC = 2    /* for batches of sources: the block products run on the tensor
                         cores with FP16 operands (power-of-two scales) and FP32
                         accumulation - one pass in the preconditioner, the three-pass
@@ -233,8 +236,12 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * PT_OPT_LEARNED: 1 = flexible GMRES adds the learned correction to the
  * preconditioner (needs learned = 1 at pt_create and weights, see below),
  * 0 = plain Algorithm 4 (default).
+ * PT_OPT_LOCAL_SOLVE: local solves of PT_MIXED_FP32 - 0 = FP32, one CTA per
+ * (layer, source) with the next column's factors staged in shared memory
+ * (default, ~1e-6 on the field); 1 = double-float on clusters of 4 CTAs
+ * (~1e-13, slower).
  * PT_ERR_ARG for an unknown option or value. */
-enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2 };
+enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3 };
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
 
 /* ---- learned preconditioner correction (not in the paper) ------------------

@@ -28,6 +28,7 @@ EXPORTS = [
 ]
 PT_OPT_LAYER_GROUP = 1
 PT_OPT_LEARNED = 2
+PT_OPT_LOCAL_SOLVE = 3
 
 
 class Params(C.Structure):

@@ -62,6 +62,8 @@ cudaError_t launch_tc_stage(const TcKey*, int, const cd*, int, int, int, int, co
 cudaError_t launch_tc_apply(int, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const CUtensorMap&,
                             const TcRow*, int, int, int, int, int, const float*, const cd*, const cd*, cd*, double,
                             double, int*, cudaStream_t);
+cudaError_t launch_layer_solve_f32(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
+                                   const cd*, const cd*, cd*, size_t, cd*, const int*, int, int*, cudaStream_t);
 cudaError_t launch_layer_solve_batch(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
                                      const cd*, const cd*, cd*, cd*, const int*, int, int, cudaStream_t);
 cudaError_t nn_forward(const __nv_bfloat16*, const float*, const float*, long, int, float*, float*, float*,
@@ -622,6 +624,7 @@ struct pt_ctx {
   __half *tc_bhi = nullptr, *tc_blo = nullptr;
   float *tc_scale = nullptr, *tc_inv = nullptr;
   int opt_layer_group = 0;  // PT_OPT_LAYER_GROUP
+  int opt_local_solve = 0;  // PT_OPT_LOCAL_SOLVE
   // learned correction
   bool nn_ready = false;    // weights set or trained
   int nn_t = 0;             // Adam steps taken
@@ -1030,6 +1033,9 @@ cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xt
   }
   if (mixed(c)) {
     if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
+    if (c->opt_local_solve == 0)  // FP32, one CTA per (layer, source)
+      return launch_layer_solve_f32(mode, P.g, c->d.layers, P.nloc_max, c->d.sinv_hi, c->d.w_hi, c->d.e_hi, f, xtr,
+                                    B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->d.status, c->stream);
     return launch_layer_solve_df(mode, P.g, c->d.layers, c->d.sinv_hi, c->d.sinv_lo, c->d.w_hi, c->d.w_lo, c->d.e_hi,
                                  c->d.e_lo, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
   }
@@ -1108,6 +1114,11 @@ extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
     if (value == 1 && !ctx->P.learned) return fail(PT_ERR_ARG, "context created with learned = 0");
     if (value == 1 && !ctx->nn_ready) return fail(PT_ERR_ARG, "no correction weights set or trained");
     ctx->opt_learned = value;
+    return PT_OK;
+  }
+  if (option == PT_OPT_LOCAL_SOLVE) {
+    if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0 or 1");
+    ctx->opt_local_solve = value;
     return PT_OK;
   }
   if (option == PT_OPT_LAYER_GROUP) {

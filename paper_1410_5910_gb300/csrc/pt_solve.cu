@@ -506,6 +506,263 @@ __global__ void __launch_bounds__(kDfThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 single-source local solve, one CTA per (layer, source), no cluster.
+// Sinv_i rounded to complex64 (the hi part of the double-float split) is
+// copied into shared memory by one bulk asynchronous copy per column (the
+// tensor-memory-access engine, completion on an mbarrier), double-buffered,
+// while the previous column computes; four threads share a row (each a quarter
+// of the columns, reduced with two shuffles) and the thread of quarter 0 keeps
+// the row's chain state, so a step needs only CTA barriers.  Accuracy: FP32
+// rounding carried through 2 n_t steps (about 1e-6 relative on the field).
+// ---------------------------------------------------------------------------
+constexpr int kF32Threads = 512;
+constexpr int kF32Q = 4;  // threads per row
+
+__device__ __forceinline__ uint32_t f32_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long f32_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for phase `parity` of an mbarrier, at most 2 s; false (and kErrTimeout) on expiry
+__device__ __forceinline__ bool f32_mb_wait(uint64_t* bar, int parity, int* status) {
+  const unsigned long long t0 = f32_timer();
+  for (long long it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(f32_saddr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && f32_timer() - t0 > 2000000000ull) break;
+  }
+  atomicOr(status, kErrTimeout);
+  return false;
+}
+
+// each Sinv buffer holds nloc_max^2 + 2 complex64 (one element of slack in front for a
+// source block that starts 8 bytes off a 16-byte boundary, one at the end), rounded to an
+// even count so that both buffers start on 16-byte boundaries (bulk-copy destinations)
+__host__ __device__ inline size_t f32_buf_elems(int nloc_max) { return ((size_t)nloc_max * nloc_max + 3) & ~(size_t)1; }
+size_t f32_solve_smem(int nloc_max) { return (2 * f32_buf_elems(nloc_max) + (size_t)kMaxNloc) * sizeof(cf); }
+
+template <int MODE>
+__global__ void __launch_bounds__(kF32Threads, 1)
+    layer_solve_f32_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cf* __restrict__ Shi,
+                           const cf* __restrict__ Whi, const cf* __restrict__ Ehi, const cd* __restrict__ f,
+                           const cd* __restrict__ xtr, cf* __restrict__ Ystore, size_t ystride, cd* __restrict__ out,
+                           const int* __restrict__ nzflag, int nmax, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int l = blockIdx.x, s = blockIdx.y;
+  const LayerInfo L = layers[l];
+  const int n = L.nloc, nt = g.nt;
+  const int T = 2 * (g.L - 1);
+  const size_t T4n = (size_t)2 * T * nt;
+  const size_t bufel = f32_buf_elems(nmax);  // even: B1 stays 16-byte aligned
+  cf* B0 = reinterpret_cast<cf*>(smem);
+  cf* B1 = B0 + bufel;
+  cf* vloc = B1 + bufel;  // [kMaxNloc]
+  const bool fnz = nzflag[s * g.L + l] != 0;
+
+  if (MODE == 0 && !fnz) {
+    cd* b = out + (size_t)s * T4n;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+      if (L.has_bot) {
+        b[(size_t)(2 * l) * nt + k] = make_double2(0, 0);
+        b[(size_t)(2 * l + 1) * nt + k] = make_double2(0, 0);
+      }
+      if (L.has_top) {
+        b[(size_t)(T + 2 * (l - 1)) * nt + k] = make_double2(0, 0);
+        b[(size_t)(T + 2 * (l - 1) + 1) * nt + k] = make_double2(0, 0);
+      }
+    }
+    return;
+  }
+
+  const int r = threadIdx.x / kF32Q, q = threadIdx.x % kF32Q;
+  const bool own = r < n && q == 0;  // owner of row r's chain state
+  const int chunk = (n + kF32Q - 1) / kF32Q;
+  const int k0 = q * chunk, k1 = min(n, k0 + chunk);
+  const cd* fs = f + (size_t)s * g.Nz * nt;
+  const cd* xs = (MODE == 1) ? xtr + (size_t)s * T4n : nullptr;
+  cf* Y = Ystore + ((size_t)s * g.L + l) * ystride;
+  const int nsteps = 2 * nt - 1;
+  auto col = [&](int st) { return st < nt ? st : nt - 2 - (st - nt); };
+  const bool in_layer = own && r >= L.pad_top && r < L.pad_top + L.n;
+  const size_t frow = in_layer ? (size_t)(L.start + r - L.pad_top) * nt : 0;
+  int ftr = -1;
+  float fsg = 0.f;
+  if (MODE == 1 && own) {
+    const float ih2 = (float)(1.0 / (g.h * g.h));
+    if (L.has_top && r == L.row[1]) { ftr = 2 * (l - 1); fsg = ih2; }
+    if (L.has_top && r == L.row[0]) { ftr = 2 * (l - 1) + 1; fsg = -ih2; }
+    if (L.has_bot && r == L.row[3]) { ftr = 2 * l; fsg = -ih2; }
+    if (L.has_bot && r == L.row[2]) { ftr = 2 * l + 1; fsg = ih2; }
+  }
+  int emit = -1;  // MODE 0: output trace of this row
+  if (MODE == 0 && own) {
+    if (L.has_bot && r == L.row[2]) emit = 2 * l;
+    if (L.has_bot && r == L.row[3]) emit = 2 * l + 1;
+    if (L.has_top && r == L.row[0]) emit = T + 2 * (l - 1);
+    if (L.has_top && r == L.row[1]) emit = T + 2 * (l - 1) + 1;
+  }
+  const int nn = n * n;
+  // the source block of column i and where its element 0 sits in the buffer
+  auto src_of = [&](int st) { return Shi + L.sinv_off + (size_t)col(st) * nn; };
+  auto view_of = [&](int st) {
+    cf* B = (st & 1) ? B1 : B0;
+    return ((reinterpret_cast<uintptr_t>(src_of(st)) & 15) != 0) ? B + 1 : B;
+  };
+
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(f32_saddr(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(f32_saddr(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // one thread: 16-byte aligned bulk part by the copy engine, an odd head / tail element by hand
+  auto stage = [&](int st) {
+    if (threadIdx.x != 0) return;
+    const cf* src = src_of(st);
+    cf* view = view_of(st);
+    const int head = (reinterpret_cast<uintptr_t>(src) & 15) ? 1 : 0;
+    const int m = nn - head;
+    const int nbulk = m & ~1;
+    if (head) view[0] = src[0];
+    if (m & 1) view[nn - 1] = src[nn - 1];
+    uint64_t* bb = &bar[st & 1];
+    const uint32_t bytes = (uint32_t)nbulk * (uint32_t)sizeof(cf);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of the buffer first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(f32_saddr(bb)), "r"(bytes)
+                 : "memory");
+    if (nbulk > 0)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              f32_saddr(view + head)),
+          "l"(src + head), "r"(bytes), "r"(f32_saddr(bb))
+          : "memory");
+  };
+  // per-row operands of a step, prefetched one step ahead by the row owner
+  cf c_next = make_float2(0.f, 0.f), y_next = make_float2(0.f, 0.f);
+  cd f_next = make_double2(0, 0), ta_next = make_double2(0, 0), tb_next = make_double2(0, 0);
+  auto prefetch = [&](int st) {
+    if (!own) return;
+    const int i = col(st);
+    const bool fwd = st < nt;
+    c_next = __ldg((fwd ? Whi : Ehi) + L.coef_off + (size_t)i * n + r);
+    if (fwd) {
+      cd v = make_double2(0, 0);
+      if (fnz && in_layer) v = fs[frow + i];
+      f_next = v;
+      if (MODE == 1 && ftr >= 0) {
+        ta_next = xs[(size_t)ftr * nt + i];
+        tb_next = xs[(size_t)(T + ftr) * nt + i];
+      }
+    } else {
+      y_next = Y[(size_t)i * n + r];
+    }
+  };
+
+  cf chain = make_float2(0.f, 0.f);  // y_{i-1} (forward) / x_{i+1} (backward) of row r
+  stage(0);
+  prefetch(0);
+  for (int st = 0; st < nsteps; ++st) {
+    const bool fwd = st < nt;
+    const int i = col(st);
+    const cf c = c_next, yst = y_next;
+    const cd fv = f_next, ta = ta_next, tb = tb_next;
+    if (st + 1 < nsteps) prefetch(st + 1);
+    // (a) right-hand side of row r
+    if (own) {
+      float vr, vi;
+      if (fwd) {
+        cd d = fv;
+        if (MODE == 1 && ftr >= 0) d = cadd(d, cscale(cadd(ta, tb), (double)fsg));
+        vr = (float)d.x;
+        vi = (float)d.y;
+        if (i > 0) {
+          vr -= c.x * chain.x - c.y * chain.y;
+          vi -= c.x * chain.y + c.y * chain.x;
+        }
+      } else {
+        vr = c.x * chain.x - c.y * chain.y;
+        vi = c.x * chain.y + c.y * chain.x;
+      }
+      vloc[r] = make_float2(vr, vi);
+    }
+    // Sinv_i in shared memory: phase (st / 2) of the buffer's barrier (bounded wait)
+    if (!f32_mb_wait(&bar[st & 1], (st >> 1) & 1, status)) return;
+    __syncthreads();  // vloc, the hand-copied elements and Sinv_i visible to all
+    if (st + 1 < nsteps) stage(st + 1);  // the other buffer was last read in step st - 1
+    // (b) row r of Sinv_i v, a quarter of the columns per thread
+    const cf* Srow = view_of(st) + (size_t)min(r, n - 1) * n;
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      const cf a0 = Srow[k], a1 = Srow[k + 1];
+      const cf v0 = vloc[k], v1 = vloc[k + 1];
+      ar = fmaf(a0.x, v0.x, ar); ar = fmaf(-a0.y, v0.y, ar);
+      ai = fmaf(a0.x, v0.y, ai); ai = fmaf(a0.y, v0.x, ai);
+      br = fmaf(a1.x, v1.x, br); br = fmaf(-a1.y, v1.y, br);
+      bi = fmaf(a1.x, v1.y, bi); bi = fmaf(a1.y, v1.x, bi);
+    }
+    if (k < k1) {
+      const cf a0 = Srow[k], v0 = vloc[k];
+      ar = fmaf(a0.x, v0.x, ar); ar = fmaf(-a0.y, v0.y, ar);
+      ai = fmaf(a0.x, v0.y, ai); ai = fmaf(a0.y, v0.x, ai);
+    }
+    ar += br;
+    ai += bi;
+    ar += __shfl_xor_sync(0xffffffffu, ar, 1);
+    ai += __shfl_xor_sync(0xffffffffu, ai, 1);
+    ar += __shfl_xor_sync(0xffffffffu, ar, 2);
+    ai += __shfl_xor_sync(0xffffffffu, ai, 2);
+    if (own) {
+      if (fwd) {
+        chain = make_float2(ar, ai);
+        Y[(size_t)i * n + r] = chain;
+      } else {
+        chain = make_float2(yst.x - ar, yst.y - ai);
+      }
+      if (!fwd || i == nt - 1) {
+        if (MODE == 0) {
+          if (emit >= 0) out[(size_t)s * T4n + (size_t)emit * nt + i] = make_double2(-(double)chain.x, -(double)chain.y);
+        } else if (in_layer) {
+          out[(size_t)s * g.Nz * nt + frow + i] = make_double2((double)chain.x, (double)chain.y);
+        }
+      }
+    }
+    __syncthreads();  // vloc is rewritten in the next step
+  }
+}
+
+// FP32 single-source local solves (grid: L CTAs x nsrc)
+cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo* layers, int nloc_max, const cf* Shi,
+                                   const cf* Whi, const cf* Ehi, const cd* f, const cd* xtr, cd* Y, size_t ystride,
+                                   cd* out, const int* flag, int nsrc, int* status, cudaStream_t s) {
+  if (nloc_max < 1 || nloc_max > kMaxNloc || nloc_max * kF32Q > kF32Threads) return cudaErrorInvalidValue;
+  const size_t smem = f32_solve_smem(nloc_max);
+  cf* Yc = reinterpret_cast<cf*>(Y);
+  dim3 grid(g.L, nsrc);
+  cudaError_t e;
+  if (mode == 0) {
+    e = cudaFuncSetAttribute(layer_solve_f32_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    layer_solve_f32_kernel<0><<<grid, kF32Threads, smem, s>>>(g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag,
+                                                              nloc_max, status);
+  } else {
+    e = cudaFuncSetAttribute(layer_solve_f32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    layer_solve_f32_kernel<1><<<grid, kF32Threads, smem, s>>>(g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag,
+                                                              nloc_max, status);
+  }
+  return cudaGetLastError();
+}
+
 // flag[s * L + l] = 1 when f^l of source s has a non-zero entry
 __global__ void layer_nonzero_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cd* __restrict__ f,
                                      int* __restrict__ flag) {

@@ -115,10 +115,25 @@ def test_mixed_fp32_preconditioner_meets_mixed_tolerance(small):
     u, tr, its, rel = solver.solve(torch.from_numpy(f).cuda(), tol=1e-9)
     mask = D.physical_mask(prob, wl.nx, wl.nz)
     assert rel[0] <= 1e-9
+    # FP32 local solves (FP64 factors rounded to complex64): ~1e-6 on the field
     assert _rel(u.cpu().numpy()[0][mask], u_ref[mask]) < 1e-5
-    # the matvec and local solves of the mixed form are double-float (~1e-13), so the
-    # field is as close to the oracle as the GMRES tolerance allows
-    assert _rel(u.cpu().numpy()[0], u_ref) < 1e-7
+    assert _rel(u.cpu().numpy()[0], u_ref) < 1e-5
+
+
+@pytest.mark.parametrize("variant,tol_field", [(0, 1e-5), (1, 1e-8)])
+def test_mixed_local_solve_variants_match_oracle(small, variant, tol_field):
+    """FP32 single-CTA local solves (default) and double-float cluster ones, on a point
+    source and on a source that excites every layer."""
+    from paper_1410_5910_gb300 import PT_OPT_LOCAL_SOLVE
+
+    wl, prob, _, off = small
+    _, solver = _mk(wl, precision=1, max_sources=2)
+    solver.set_option(PT_OPT_LOCAL_SOLVE, variant)
+    f = np.concatenate([wl.f(), W.random_sources(wl.nt, wl.Nz, wl.npml, wl.nx, wl.nz, 9, 1)])
+    u, tr, its, rel = solver.solve(torch.from_numpy(f).cuda(), tol=1e-10)
+    for s in range(2):
+        assert rel[s] <= 1e-10
+        assert _rel(u.cpu().numpy()[s], S.global_solve(prob, f[s])) < tol_field
 
 
 def test_batched_sources_equal_single_solves():

@@ -160,7 +160,13 @@ GRF_511x1023 = Workload("grf-511x1023-L16", 511, 1023, 20, 16, 10.0, "grf", 2, (
 LAYERED_1023x2047 = Workload("layered-1023x2047-L32", 1023, 2047, 20, 32, 10.0, "layered", 3,
                              tuple((2 + 4 * s, 1) for s in range(256)), 1e-7)
 
-WORKLOADS = {w.name: w for w in (CONSTANT_128, GRF_511x1023, LAYERED_1023x2047)}
+# The layered family at a quarter of the size (255 x 511, L = 8, 64 sources on the first
+# physical row): the same local-problem and block shapes per layer at ~1 GB of device
+# memory, for kernel captures under a profiler.
+LAYERED_255x511 = Workload("layered-255x511-L8", 255, 511, 20, 8, 10.0, "layered", 3,
+                           tuple((2 + 4 * s, 1) for s in range(64)), 1e-7)
+
+WORKLOADS = {w.name: w for w in (CONSTANT_128, GRF_511x1023, LAYERED_1023x2047, LAYERED_255x511)}
 
 
 def small_case(nx: int, nz: int, npml: int, L: int, ppw: float = 10.0, medium: str = "constant", seed: int = 0,
