@@ -326,7 +326,8 @@ def main():
 
     import torch
 
-    from paper_1410_5910_gb300 import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PolarTrace, default_pml_strength
+    from paper_1410_5910_gb300 import (PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PolarTrace, default_pml_strength,
+                                       layer_partition)
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -401,8 +402,52 @@ def main():
             del ps
             torch.cuda.empty_cache()
 
-    # ---- roofline of the block-apply kernel (the interface-system matvec, one launch) ----
+    # ---- roofline of the dominant kernel of the chosen form ----
     pk, pk_kind = peaks()
+    L_ = wl.L
+    nt = wl.nt
+    nb = [int(v) for v in np.diff(np.asarray(layer_partition(wl.nx, wl.nz, wl.npml, L_)))]
+    nloc = [n_ + (wl.npml if l_ > 0 else 0) + (wl.npml if l_ < L_ - 1 else 0) for l_, n_ in enumerate(nb)]
+    if chosen_prec == PT_MIXED_FP32:
+        # local solves (reconstruction launch: every layer, 2 n_t - 1 dependent steps), timed live as the
+        # difference of solves with and without the volume output
+        u_tmp = torch.empty_like(f_dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        t_with, t_without = [], []
+        for _ in range(5):
+            ev[0][0].record(stream)
+            solver.solve(f_dev, tol=tol, u=u_tmp, want_traces=False)
+            ev[0][1].record(stream)
+            ev[1][0].record(stream)
+            solver.solve(f_dev, tol=tol, want_u=False, want_traces=False)
+            ev[1][1].record(stream)
+            torch.cuda.synchronize(dev)
+            t_with.append(ev[0][0].elapsed_time(ev[0][1]))
+            t_without.append(ev[1][0].elapsed_time(ev[1][1]))
+        t_launch = (statistics.median(t_with) - statistics.median(t_without)) / 1e3
+        # algorithmic bytes per launch: Sinv (complex64) of every column of every layer, read by the forward
+        # and again by the backward substitution (2 n_t - 1 column steps), the x-couplings, the forward
+        # iterates written and read back (complex64), the volume output and the trace forcing
+        steps = 2 * nt - 1
+        sinv = sum(steps * n_ * n_ * 8 for n_ in nloc)
+        coef = sum(2 * nt * n_ * 8 for n_ in nloc)
+        ystore = sum(2 * nt * n_ * 8 for n_ in nloc)
+        vol = wl.Nz * nt * 16 + 4 * (L_ - 1) * nt * 16
+        alg = (sinv + coef + ystore + vol) * S
+        # DRAM traffic of the same kernel on the 255 x 511, L = 8 layered case (ncu): 0.79 x its
+        # algorithmic bytes (L2 serves the columns around the forward / backward turn); traffic grows
+        # with the units (column steps x rows^2), so it is scaled
+        traffic = 0.79 * alg
+        roof = {"kernel": "layer_solve_f32_kernel<1> (FP32 local solves, reconstruction of every layer)",
+                "bound": "hbm", "achieved": alg / t_launch / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": traffic, "algorithmic_bytes": alg, "launch_ms": t_launch * 1e3,
+                "latency_bound": f"{steps} dependent column steps, {t_launch / steps * 1e6:.2f} us per step",
+                "achieved_gflops": 8.0 * sum(n_ * n_ for n_ in nloc) * steps * S / t_launch / 1e9,
+                "traffic_source": "scaled from the ncu capture of the layered-255x511-L8 case"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        roof = None
+    # the interface-system matvec with FP64 blocks (the plain form's GEMV), one launch
     x = torch.randn((S, fp64_solver.T4, fp64_solver.nt), dtype=torch.complex128, device=dev)
     for _ in range(3):
         fp64_solver.matvec(x)
@@ -412,17 +457,17 @@ def main():
         fp64_solver.matvec(x)
         b_.record(stream)
     torch.cuda.synchronize(dev)
-    t_launch = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
-    L_ = wl.L
+    t_mv = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
     nblocks = 16 * (L_ - 2) + 8
-    nt = wl.nt
     flops = 8.0 * nblocks * nt * nt * S
-    roof = {"kernel": "apply_kernel<double2> (interface-system matvec P M x, FP64 blocks)", "bound": "alu",
-            "achieved": flops / t_launch / 1e12, "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
-            "frac": None, "traffic": None, "peak_source": "FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz",
-            "algorithmic_bytes": nblocks * nt * nt * 16 + 2 * 4 * (L_ - 1) * nt * 16 * S,
-            "achieved_hbm_gbs": (nblocks * nt * nt * 16) / t_launch / 1e9, "launch_ms": t_launch * 1e3}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof64 = {"kernel": "apply_kernel<double2> (interface-system matvec P M x, FP64 blocks)", "bound": "alu",
+              "achieved": flops / t_mv / 1e12, "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
+              "frac": None, "traffic": None, "peak_source": "FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz",
+              "algorithmic_bytes": nblocks * nt * nt * 16 + 2 * 4 * (L_ - 1) * nt * 16 * S,
+              "achieved_hbm_gbs": (nblocks * nt * nt * 16) / t_mv / 1e9, "launch_ms": t_mv * 1e3}
+    roof64["frac"] = roof64["achieved"] / roof64["peak"]
+    if roof is None:
+        roof = roof64
 
     # ---- end to end through the host-buffer entry point (pinned memory) ----
     f_pin = torch.from_numpy(f_host).pin_memory()
@@ -465,7 +510,8 @@ def main():
                        "l2": f"interface blocks {16 * L_ * nt * nt * 16 / 1e9:.2f} GB stream from HBM each "
                              "iteration (> 129 MB L2); no flush needed"},
             "gmres_iterations": its, "true_relres": rel, "offline_s": t_off,
-            "roofline": roof, "peaks_source": pk_kind, "clocks": clocks, "e2e": e2e,
+            "roofline": roof, "roofline_fp64_matvec": roof64, "peaks_source": pk_kind, "clocks": clocks,
+            "e2e": e2e,
             "gpu_launches": int(launches * args.steps), "cpu_baseline": cpu,
         }
         if plain is not None:
