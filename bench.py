@@ -263,6 +263,58 @@ def batched_section(args, dev, pg, pk):
     return out
 
 
+def uneven_section(args, dev, pg):
+    """Uneven batch: independent problems of the GRF family with different sizes, layer counts and source
+    counts (mixed form), solved one instance after another and concurrently (pt_solve_many, one stream per
+    instance).  Offline phases excluded."""
+    import torch
+
+    from paper_1410_5910_gb300 import PT_MIXED_FP32, PolarTrace, default_pml_strength, solve_many
+
+    cases = W.uneven_batch(count=args.uneven_count, nmin=255, nmax=args.uneven_nmax, Lmin=8, Lmax=16)
+    solvers, fs = [], []
+    t0 = time.perf_counter()
+    for wl in cases:
+        c = wl.c_ext()
+        om = wl.omega(c)
+        sv = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, om, torch.from_numpy(c).to(dev),
+                        pml_C=default_pml_strength(float(c.max())), precision=PT_MIXED_FP32,
+                        max_sources=len(wl.sources), max_krylov=40, stream=torch.cuda.Stream(dev))
+        solvers.append(sv)
+        fs.append(torch.from_numpy(wl.f()).to(dev))
+    torch.cuda.synchronize(dev)
+    t_off = time.perf_counter() - t0
+    nsol = sum(f.shape[0] for f in fs)
+
+    def sequential():
+        for sv, f in zip(solvers, fs):
+            sv.solve(f, tol=1e-7, want_traces=False)
+        torch.cuda.synchronize(dev)
+
+    def concurrent():
+        return solve_many(solvers, fs, tol=1e-7)
+
+    out = {"instances": len(cases), "sources": nsol, "offline_s": t_off,
+           "n_range": [min(w.nx for w in cases), max(w.nx for w in cases)],
+           "L_range": [min(w.L for w in cases), max(w.L for w in cases)],
+           "form": "mixed, one stream and one host thread per instance"}
+    for name, fn in (("sequential", sequential), ("concurrent", concurrent)):
+        fn()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.uneven_steps):
+            r = fn()
+        dt = max_over_ranks(pg, (time.perf_counter() - t0) / args.uneven_steps)
+        out[name] = {"value": nsol / dt, "unit": "solves/s", "ms_per_batch": dt * 1e3}
+        if name == "concurrent":
+            out["gmres_iterations_max"] = max(max(i) for i in r[1])
+            out["true_relres_max"] = max(max(x) for x in r[2])
+    out["value"] = out["concurrent"]["value"]
+    del solvers, fs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, wl, rank, world, pg):
     """--impl reference: the CPU oracle timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -314,6 +366,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core form (256 sources)")
     ap.add_argument("--batched-sources", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven batch of independent problems")
+    ap.add_argument("--uneven-count", type=int, default=16)
+    ap.add_argument("--uneven-nmax", type=int, default=511)
+    ap.add_argument("--uneven-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -488,6 +544,10 @@ def main():
         del solver, fp64_solver, scratch
         torch.cuda.empty_cache()
         batched = batched_section(args, dev, pg, pk)
+    uneven = None
+    if not args.no_uneven:
+        torch.cuda.empty_cache()
+        uneven = uneven_section(args, dev, pg)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -518,6 +578,8 @@ def main():
             line["plain_fp64"] = plain
         if batched is not None:
             line["batched"] = batched
+        if uneven is not None:
+            line["uneven"] = uneven
         line.update(plr_results)
         line.update(extra)
         print(json.dumps(line), flush=True)

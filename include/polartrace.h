@@ -298,6 +298,18 @@ pt_status pt_apply_correction(pt_ctx* ctx, int32_t nsrc, const pt_c128* v, pt_c1
  * of the layer's interfaces.  Fails with PT_ERR_ARG otherwise. */
 pt_status pt_get_block(pt_ctx* ctx, int32_t layer, int32_t j, int32_t k, pt_c128* dst);
 
+/* Uneven batch: independent contexts (different media, grids, layer counts
+ * and source counts), each solved as by pt_solve, concurrently - one host
+ * thread per context, each context on its own stream (contexts created on
+ * the same stream serialise).  Arrays of length nctx: ctxs (distinct),
+ * nsrc, f (device), u (device, or u = NULL for no volume output), scratch,
+ * scratch_bytes.  iters and relres (host, NULL allowed) hold sum(nsrc)
+ * entries, context after context; status (host, NULL allowed) nctx.
+ * Returns the first failing context's status (its index in the error text). */
+pt_status pt_solve_many(int32_t nctx, pt_ctx* const* ctxs, const int32_t* nsrc, const pt_c128* const* f,
+                        pt_c128* const* u, double rel_tol, int32_t max_it, void* const* scratch,
+                        const size_t* scratch_bytes, int32_t* iters, double* relres, int32_t* status);
+
 /* Statistics of the last pt_solve: number of kernel launches it issued and
  * the GMRES iteration count of the slowest source. */
 pt_status pt_last_solve_stats(const pt_ctx* ctx, int64_t* kernel_launches, int32_t* max_iterations);

@@ -18,7 +18,7 @@ import torch
 
 from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, PT_OPT_LEARNED, PT_OPT_LOCAL_SOLVE, Params, PolarTraceError, check, lib
 
-__all__ = ["PolarTrace", "PolarTraceError", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "PT_OPT_LOCAL_SOLVE", "default_pml_strength",
+__all__ = ["PolarTrace", "PolarTraceError", "solve_many", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "PT_OPT_LOCAL_SOLVE", "default_pml_strength",
            "layer_partition"]
 
 
@@ -43,6 +43,41 @@ def layer_partition(nx, nz, npml, L) -> list:
 
 def _ptr(t: torch.Tensor) -> int:
     return t.data_ptr()
+
+
+def solve_many(solvers, fs, tol: float = 1e-7, max_it: int | None = None, want_u: bool = True):
+    """Uneven batch: solve every solver's sources concurrently (pt_solve_many).  Give each solver its own
+    stream (PolarTrace(..., stream=torch.cuda.Stream())) for the solves to overlap.  Returns
+    (u list, iterations list, true relative residual list)."""
+    n = len(solvers)
+    if n != len(fs):
+        raise ValueError("one source tensor per solver")
+    us = []
+    for sv, f in zip(solvers, fs):
+        sv._check_src(f)
+        us.append(torch.empty_like(f) if want_u else None)
+    if max_it is None:
+        max_it = min(sv.max_krylov for sv in solvers)
+    vp = C.c_void_p
+    ctxs = (vp * n)(*[sv._ctx.value for sv in solvers])
+    nsrc = (C.c_int32 * n)(*[f.shape[0] for f in fs])
+    fp = (vp * n)(*[f.data_ptr() for f in fs])
+    up = (vp * n)(*[u.data_ptr() for u in us]) if want_u else None
+    scr = (vp * n)(*[sv._scratch.data_ptr() for sv in solvers])
+    scb = (C.c_size_t * n)(*[sv._scratch.numel() for sv in solvers])
+    tot = sum(f.shape[0] for f in fs)
+    iters = (C.c_int32 * tot)()
+    rel = (C.c_double * tot)()
+    status = (C.c_int32 * n)()
+    torch.cuda.synchronize()
+    check(lib().pt_solve_many(n, ctxs, nsrc, fp, up, tol, max_it, scr, scb, iters, rel, status), "pt_solve_many")
+    torch.cuda.synchronize()
+    out_i, out_r, o = [], [], 0
+    for f in fs:
+        out_i.append(list(iters[o:o + f.shape[0]]))
+        out_r.append(list(rel[o:o + f.shape[0]]))
+        o += f.shape[0]
+    return us, out_i, out_r
 
 
 class PolarTrace:

@@ -19,6 +19,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/polartrace.h"
@@ -1656,6 +1657,43 @@ extern "C" pt_status pt_solve(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c1
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
   return solve_impl(ctx, nsrc, reinterpret_cast<const cd*>(f), reinterpret_cast<cd*>(u),
                     reinterpret_cast<cd*>(traces), rel_tol, max_it, B, iters, relres);
+}
+
+extern "C" pt_status pt_solve_many(int32_t nctx, pt_ctx* const* ctxs, const int32_t* nsrc, const pt_c128* const* f,
+                                   pt_c128* const* u, double rel_tol, int32_t max_it, void* const* scratch,
+                                   const size_t* scratch_bytes, int32_t* iters, double* relres, int32_t* status) {
+  if (nctx < 1 || !ctxs || !nsrc || !f || !scratch || !scratch_bytes) return fail(PT_ERR_ARG, "bad arguments");
+  std::vector<size_t> off(nctx + 1, 0);
+  for (int k = 0; k < nctx; ++k) {
+    if (!ctxs[k]) return fail(PT_ERR_ARG, "a context is NULL");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(PT_ERR_ARG, "a context appears twice");
+    if (nsrc[k] < 1) return fail(PT_ERR_ARG, "nsrc must be >= 1");
+    off[k + 1] = off[k] + (size_t)nsrc[k];
+  }
+  int dev = 0;
+  PT_CUDA(cudaGetDevice(&dev));
+  std::vector<pt_status> st(nctx, PT_OK);
+  std::vector<std::string> msg(nctx);
+  auto work = [&](int k) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      st[k] = PT_ERR_CUDA;
+      msg[k] = "cudaSetDevice failed";
+      return;
+    }
+    st[k] = pt_solve(ctxs[k], nsrc[k], f[k], u ? u[k] : nullptr, nullptr, rel_tol, max_it, scratch[k],
+                     scratch_bytes[k], iters ? iters + off[k] : nullptr, relres ? relres + off[k] : nullptr);
+    if (st[k] != PT_OK) msg[k] = pt_last_error();
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nctx);
+  for (int k = 0; k < nctx; ++k) pool.emplace_back(work, k);
+  for (auto& t : pool) t.join();
+  if (status)
+    for (int k = 0; k < nctx; ++k) status[k] = (int32_t)st[k];
+  for (int k = 0; k < nctx; ++k)
+    if (st[k] != PT_OK) return fail(st[k], ("context " + std::to_string(k) + ": " + msg[k]).c_str());
+  return PT_OK;
 }
 
 extern "C" pt_status pt_solve_host(pt_ctx* ctx, int32_t nsrc, const pt_c128* f_host, pt_c128* u_host,

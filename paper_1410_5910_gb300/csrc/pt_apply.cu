@@ -259,15 +259,15 @@ cudaError_t launch_apply_mode(int mode, int nt, int ld, int T4, const ApplyRow* 
   dim3 grid(nsrc, (nt + rows_per_cta - 1) / rows_per_cta, nrows);
   cudaError_t e = cudaSuccess;
   if (mode == kFP64) {
-    e = cudaFuncSetAttribute(apply_kernel<kFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(apply_kernel<kFP64>));
     apply_kernel<kFP64><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, x, aux, y, rows_per_cta,
                                                 alpha, beta);
   } else if (mode == kFP32) {
-    e = cudaFuncSetAttribute(apply_kernel<kFP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(apply_kernel<kFP32>));
     apply_kernel<kFP32><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, x, aux, y, rows_per_cta,
                                                 alpha, beta);
   } else {
-    e = cudaFuncSetAttribute(apply_kernel<kDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(apply_kernel<kDF>));
     apply_kernel<kDF><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, x, aux, y, rows_per_cta,
                                               alpha, beta);
   }

@@ -312,8 +312,7 @@ static cudaError_t go_batch(const Geometry& g, const LayerInfo* layers, int nloc
   int dbuf = 0;
   const size_t smem = batch_smem_bytes(nloc_max, GW, RW * kBatchWarps * (32 / GW), &dbuf);
   if (smem > kBatchSmemMax) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(layer_solve_batch_kernel<MODE, GW, RW>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit_max(reinterpret_cast<const void*>(layer_solve_batch_kernel<MODE, GW, RW>));
   if (e != cudaSuccess) return e;
   const size_t ylayer = (size_t)g.nt * nloc_max * GW;
   dim3 grid(g.L, (nsrc + GW - 1) / GW);

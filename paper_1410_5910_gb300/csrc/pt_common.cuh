@@ -14,7 +14,30 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <unordered_set>
+
 namespace pt {
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum (less its
+// static shared memory), once per kernel.  The limit is a per-function setting: setting
+// it to each launch's own size would race between host threads that launch the same
+// kernel with different sizes (independent solves on concurrent streams).
+inline cudaError_t smem_limit_max(const void* kernel) {
+  static std::mutex m;
+  static std::unordered_set<const void*> done;
+  std::lock_guard<std::mutex> guard(m);
+  if (done.count(kernel)) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert(kernel);
+  return e;
+}
 
 typedef double2 cd;
 typedef float2 cf;

@@ -289,7 +289,7 @@ cudaError_t launch_coef(const Geometry& g, const LayerInfo* layers, const double
 cudaError_t launch_factor(const Geometry& g, const LayerInfo* layers, int nloc_max, const double* c, cd* Sinv,
                           int* status, cudaStream_t s) {
   size_t smem = (size_t)nloc_max * nloc_max * sizeof(cd) + 6ull * nloc_max * sizeof(cd) + nloc_max * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit_max(reinterpret_cast<const void*>(factor_kernel));
   if (e != cudaSuccess) return e;
   factor_kernel<<<g.L, 512, smem, s>>>(g, layers, c, Sinv, status);
   return cudaGetLastError();
@@ -299,7 +299,7 @@ cudaError_t launch_extract(const Geometry& g, const LayerInfo* layers, const Ext
                            int nslots, int nloc_max, const cd* Sinv, const cd* W, const cd* E, cd* Y,
                            size_t slot_elems, cd* blocks, cudaStream_t s) {
   size_t smem = 2ull * nloc_max * 32 * sizeof(cd);
-  cudaError_t e = cudaFuncSetAttribute(extract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit_max(reinterpret_cast<const void*>(extract_kernel));
   if (e != cudaSuccess) return e;
   extract_kernel<<<nslots, 256, smem, s>>>(g, layers, tasks, ntasks, Sinv, W, E, Y, slot_elems, blocks);
   return cudaGetLastError();

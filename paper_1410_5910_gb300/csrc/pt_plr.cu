@@ -475,7 +475,7 @@ cudaError_t launch_plr_compress(int nt, const cd* blocks, const int* block_ids, 
                                 int oversample, cd* scratch, int nslots, PlrLeaf* leaves, int cap, int* nleaves,
                                 cd* pool, int* status, cudaStream_t s) {
   const size_t smem = 2ull * kPlrK * kPlrK * sizeof(cd);
-  cudaError_t e = cudaFuncSetAttribute(plr_compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit_max(reinterpret_cast<const void*>(plr_compress_kernel));
   if (e != cudaSuccess) return e;
   plr_compress_kernel<<<nslots, kPlrThreads, smem, s>>>(nt, blocks, block_ids, nblk, rmax, eps, oversample, scratch,
                                                         plr_scratch_per_cta(nt), leaves, cap, nleaves, pool, status);
@@ -501,13 +501,13 @@ cudaError_t launch_plr_apply(bool fp32, int nt, int T4, int /*ldd*/, const Apply
   dim3 g2(ntiles, nrows, nsrc);
   cudaError_t e;
   if (fp32) {
-    e = cudaFuncSetAttribute(plr_expand_kernel<cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(plr_expand_kernel<cf>));
     plr_expand_kernel<cf><<<g2, 32 * kExpWarps, smem, s>>>(nt, T4, table, (const cf*)pool, leaves, tile_ptr,
                                                            tile_leaf, ntiles, task_base, lr_ord,
                                                            reinterpret_cast<const cf*>(tbuf), ntasks, rmax, x, aux, y,
                                                            alpha, beta);
   } else {
-    e = cudaFuncSetAttribute(plr_expand_kernel<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(plr_expand_kernel<cd>));
     plr_expand_kernel<cd><<<g2, 32 * kExpWarps, smem, s>>>(nt, T4, table, (const cd*)pool, leaves, tile_ptr,
                                                            tile_leaf, ntiles, task_base, lr_ord, tbuf, ntasks, rmax, x,
                                                            aux, y, alpha, beta);

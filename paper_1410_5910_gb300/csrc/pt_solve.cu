@@ -750,12 +750,12 @@ cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo*
   dim3 grid(g.L, nsrc);
   cudaError_t e;
   if (mode == 0) {
-    e = cudaFuncSetAttribute(layer_solve_f32_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(layer_solve_f32_kernel<0>));
     if (e != cudaSuccess) return e;
     layer_solve_f32_kernel<0><<<grid, kF32Threads, smem, s>>>(g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag,
                                                               nloc_max, status);
   } else {
-    e = cudaFuncSetAttribute(layer_solve_f32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(layer_solve_f32_kernel<1>));
     if (e != cudaSuccess) return e;
     layer_solve_f32_kernel<1><<<grid, kF32Threads, smem, s>>>(g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag,
                                                               nloc_max, status);

@@ -363,17 +363,17 @@ cudaError_t launch_tc_apply(int bn, const CUtensorMap& ahi, const CUtensorMap& a
   const size_t smem = tc_smem_bytes(bn);
   cudaError_t e;
   if (bn == 64) {
-    e = cudaFuncSetAttribute(tc_apply_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(tc_apply_kernel<64>));
     if (e == cudaSuccess)
       tc_apply_kernel<64><<<grid, 128, smem, s>>>(ahi, alo, bhi, blo, rows, nt, T4, S, npass, inv, x, aux, y, alpha,
                                                  beta, status);
   } else if (bn == 128) {
-    e = cudaFuncSetAttribute(tc_apply_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(tc_apply_kernel<128>));
     if (e == cudaSuccess)
       tc_apply_kernel<128><<<grid, 128, smem, s>>>(ahi, alo, bhi, blo, rows, nt, T4, S, npass, inv, x, aux, y, alpha,
                                                   beta, status);
   } else {
-    e = cudaFuncSetAttribute(tc_apply_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max(reinterpret_cast<const void*>(tc_apply_kernel<256>));
     if (e == cudaSuccess)
       tc_apply_kernel<256><<<grid, 128, smem, s>>>(ahi, alo, bhi, blo, rows, nt, T4, S, npass, inv, x, aux, y, alpha,
                                                   beta, status);

@@ -169,6 +169,32 @@ LAYERED_255x511 = Workload("layered-255x511-L8", 255, 511, 20, 8, 10.0, "layered
 WORKLOADS = {w.name: w for w in (CONSTANT_128, GRF_511x1023, LAYERED_1023x2047, LAYERED_255x511)}
 
 
+def uneven_batch(count: int = 64, seed: int = 4, nmin: int = 255, nmax: int = 1023, Lmin: int = 8, Lmax: int = 32,
+                 npml: int = 20, smax: int = 16, max_local_rows: int = 118) -> list:
+    """An uneven batch of independent problems of the GRF family: n ~ U{nmin..nmax} odd, n_z = 2 n + 1,
+    medium seed 4000 + i, ppw ~ U[8, 12] at c_min, L ~ U{Lmin..Lmax} capped so that every layer has
+    npml + 2 rows and raised so that every padded local problem has at most max_local_rows rows,
+    1..smax point sources in the top 10 % of the physical rows, tolerance 1e-7."""
+    g = rng(seed)
+    out = []
+    for i in range(count):
+        n = int(g.integers(nmin // 2, nmax // 2 + 1)) * 2 + 1
+        n = min(max(n, nmin | 1), nmax)
+        nz = 2 * n + 1
+        # the near-equal split keeps the first and last interfaces outside the PML only when every
+        # layer has at least npml + 2 rows
+        # ... and the local problems (layer rows + 2 npml padded rows) fit the library's limit
+        Nz = nz + 2 * npml
+        L = min(int(g.integers(Lmin, Lmax + 1)), Nz // (npml + 2))
+        L = max(L, -(-Nz // (max_local_rows - 2 * npml - 1)))
+        ppw = float(g.uniform(8.0, 12.0))
+        ns = int(g.integers(1, smax + 1))
+        top = max(2, nz // 10)
+        src = tuple((int(g.integers(1, n + 1)), int(g.integers(1, top + 1))) for _ in range(ns))
+        out.append(Workload(f"grf-{n}x{nz}-L{L}-i{i}", n, nz, npml, L, ppw, "grf", 4000 + i, src, 1e-7))
+    return out
+
+
 def small_case(nx: int, nz: int, npml: int, L: int, ppw: float = 10.0, medium: str = "constant", seed: int = 0,
                sources=None, tol: float = 1e-10) -> Workload:
     """A reduced workload of the same structure for tests."""
