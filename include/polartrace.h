@@ -236,10 +236,11 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * PT_OPT_LEARNED: 1 = flexible GMRES adds the learned correction to the
  * preconditioner (needs learned = 1 at pt_create and weights, see below),
  * 0 = plain Algorithm 4 (default).
- * PT_OPT_LOCAL_SOLVE: local solves of PT_MIXED_FP32 - 0 = FP32, one CTA per
- * (layer, source) with the next column's factors staged in shared memory
- * (default, ~1e-6 on the field); 1 = double-float on clusters of 4 CTAs
- * (~1e-13, slower).
+ * PT_OPT_LOCAL_SOLVE: local solves of PT_MIXED_FP32 - 0 = FP32 on a cluster
+ * of 4 CTAs per (layer, source), each CTA holding a quarter of the rows of
+ * the next column's factors in shared memory (default, ~1e-6 on the field);
+ * 3 = the same on 8 CTAs; 2 = FP32 on one CTA; 1 = double-float on clusters
+ * of 4 CTAs (~1e-13, slower).
  * PT_ERR_ARG for an unknown option or value. */
 enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3 };
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);

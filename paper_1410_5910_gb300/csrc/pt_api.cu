@@ -64,7 +64,7 @@ cudaError_t launch_tc_apply(int, const CUtensorMap&, const CUtensorMap&, const C
                             const TcRow*, int, int, int, int, int, const float*, const cd*, const cd*, cd*, double,
                             double, int*, cudaStream_t);
 cudaError_t launch_layer_solve_f32(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
-                                   const cd*, const cd*, cd*, size_t, cd*, const int*, int, int*, cudaStream_t);
+                                   const cd*, const cd*, cd*, size_t, cd*, const int*, int, int*, int, cudaStream_t);
 cudaError_t launch_layer_solve_batch(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
                                      const cd*, const cd*, cd*, cd*, const int*, int, int, cudaStream_t);
 cudaError_t nn_forward(const __nv_bfloat16*, const float*, const float*, long, int, float*, float*, float*,
@@ -1034,9 +1034,10 @@ cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xt
   }
   if (mixed(c)) {
     if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
-    if (c->opt_local_solve == 0)  // FP32, one CTA per (layer, source)
+    if (c->opt_local_solve != 1)  // FP32 on a cluster of 4 (0) or 8 (3) CTAs, or one CTA (2), per (layer, source)
       return launch_layer_solve_f32(mode, P.g, c->d.layers, P.nloc_max, c->d.sinv_hi, c->d.w_hi, c->d.e_hi, f, xtr,
-                                    B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->d.status, c->stream);
+                                    B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->d.status,
+                                    c->opt_local_solve == 0 ? 4 : (c->opt_local_solve == 3 ? 8 : 1), c->stream);
     return launch_layer_solve_df(mode, P.g, c->d.layers, c->d.sinv_hi, c->d.sinv_lo, c->d.w_hi, c->d.w_lo, c->d.e_hi,
                                  c->d.e_lo, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
   }
@@ -1118,7 +1119,7 @@ extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
     return PT_OK;
   }
   if (option == PT_OPT_LOCAL_SOLVE) {
-    if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0 or 1");
+    if (value < 0 || value > 3) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0, 1, 2 or 3");
     ctx->opt_local_solve = value;
     return PT_OK;
   }

@@ -740,15 +740,267 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   }
 }
 
-// FP32 single-source local solves (grid: L CTAs x nsrc)
+// ---------------------------------------------------------------------------
+// FP32 local solve on a cluster of CS CTAs per (layer, source): CTA c owns the
+// rows [c rpc, (c + 1) rpc) of the local problem, copies only its rows of each
+// column's Schur inverse (one bulk copy per column and CTA, double-buffered)
+// and computes only their products; the owners of the right-hand-side entries
+// v_r broadcast them to every CTA of the cluster through distributed shared
+// memory (double-buffered by step parity), one cluster barrier per step.
+// The per-row operands of the next step are loaded after the barrier, so its
+// release never waits for loads in flight.
+// ---------------------------------------------------------------------------
+constexpr int kF32cQ = 8;         // threads per row
+constexpr int kF32cThreads = 256;
+
+template <int CS>
+struct F32cLayout {
+  static constexpr int RPC = (kMaxNloc + CS - 1) / CS;
+  // Sinv slice buffers: RPC * kMaxNloc + 2 complex64 each, even count (16-byte aligned)
+  static constexpr size_t buf = ((size_t)RPC * kMaxNloc + 3) & ~(size_t)1;
+  static constexpr size_t bytes = (2 * buf + 2 * (size_t)kMaxNloc) * sizeof(cf);
+};
+
+template <int MODE, int CS>
+__global__ void __launch_bounds__(kF32cThreads, 1)
+    layer_solve_f32c_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cf* __restrict__ Shi,
+                            const cf* __restrict__ Whi, const cf* __restrict__ Ehi, const cd* __restrict__ f,
+                            const cd* __restrict__ xtr, cf* __restrict__ Ystore, size_t ystride,
+                            cd* __restrict__ out, const int* __restrict__ nzflag, int* __restrict__ status) {
+  using Lay = F32cLayout<CS>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int l = blockIdx.x / CS, s = blockIdx.y;
+  const LayerInfo L = layers[l];
+  const int n = L.nloc, nt = g.nt;
+  const int T = 2 * (g.L - 1);
+  const size_t T4n = (size_t)2 * T * nt;
+  cf* B0 = reinterpret_cast<cf*>(smem);
+  cf* B1 = B0 + Lay::buf;
+  cf* vbuf = B1 + Lay::buf;  // [2][kMaxNloc], written by every CTA of the cluster
+  const bool fnz = nzflag[s * g.L + l] != 0;
+  const int rpc = (n + CS - 1) / CS;
+  const int r0 = rank * rpc, r1 = min(n, r0 + rpc);
+
+  if (MODE == 0 && !fnz) {  // uniform over the cluster, before any cluster barrier
+    cd* b = out + (size_t)s * T4n;
+    for (int k = rank * blockDim.x + threadIdx.x; k < nt; k += CS * blockDim.x) {
+      if (L.has_bot) {
+        b[(size_t)(2 * l) * nt + k] = make_double2(0, 0);
+        b[(size_t)(2 * l + 1) * nt + k] = make_double2(0, 0);
+      }
+      if (L.has_top) {
+        b[(size_t)(T + 2 * (l - 1)) * nt + k] = make_double2(0, 0);
+        b[(size_t)(T + 2 * (l - 1) + 1) * nt + k] = make_double2(0, 0);
+      }
+    }
+    return;
+  }
+
+  const int lr = threadIdx.x / kF32cQ, q = threadIdx.x % kF32cQ;  // local row, column chunk
+  const int r = r0 + lr;
+  const bool own = r < r1 && q == 0;
+  const int chunk = (n + kF32cQ - 1) / kF32cQ;
+  const int k0 = q * chunk, k1 = min(n, k0 + chunk);
+  const cd* fs = f + (size_t)s * g.Nz * nt;
+  const cd* xs = (MODE == 1) ? xtr + (size_t)s * T4n : nullptr;
+  cf* Y = Ystore + ((size_t)s * g.L + l) * ystride;
+  const int nsteps = 2 * nt - 1;
+  auto col = [&](int st) { return st < nt ? st : nt - 2 - (st - nt); };
+  const bool in_layer = own && r >= L.pad_top && r < L.pad_top + L.n;
+  const size_t frow = in_layer ? (size_t)(L.start + r - L.pad_top) * nt : 0;
+  int ftr = -1;
+  float fsg = 0.f;
+  if (MODE == 1 && own) {
+    const float ih2 = (float)(1.0 / (g.h * g.h));
+    if (L.has_top && r == L.row[1]) { ftr = 2 * (l - 1); fsg = ih2; }
+    if (L.has_top && r == L.row[0]) { ftr = 2 * (l - 1) + 1; fsg = -ih2; }
+    if (L.has_bot && r == L.row[3]) { ftr = 2 * l; fsg = -ih2; }
+    if (L.has_bot && r == L.row[2]) { ftr = 2 * l + 1; fsg = ih2; }
+  }
+  int emit = -1;
+  if (MODE == 0 && own) {
+    if (L.has_bot && r == L.row[2]) emit = 2 * l;
+    if (L.has_bot && r == L.row[3]) emit = 2 * l + 1;
+    if (L.has_top && r == L.row[0]) emit = T + 2 * (l - 1);
+    if (L.has_top && r == L.row[1]) emit = T + 2 * (l - 1) + 1;
+  }
+  const int cnt = (r1 - r0) * n;  // this CTA's slice of a column: contiguous rows r0 .. r1 - 1
+  auto src_of = [&](int st) { return Shi + L.sinv_off + (size_t)col(st) * n * n + (size_t)r0 * n; };
+  auto view_of = [&](int st) {
+    cf* B = (st & 1) ? B1 : B0;
+    return ((reinterpret_cast<uintptr_t>(src_of(st)) & 15) != 0) ? B + 1 : B;
+  };
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(f32_saddr(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(f32_saddr(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // every call arms the buffer's barrier (zero bytes for a CTA that owns no rows)
+  auto stage = [&](int st) {
+    if (threadIdx.x != 0) return;
+    const cf* src = src_of(st);
+    cf* view = view_of(st);
+    const int head = (cnt > 0 && (reinterpret_cast<uintptr_t>(src) & 15)) ? 1 : 0;
+    const int m = cnt > 0 ? cnt - head : 0;
+    const int nbulk = m & ~1;
+    if (head) view[0] = src[0];
+    if (m & 1) view[cnt - 1] = src[cnt - 1];
+    uint64_t* bb = &bar[st & 1];
+    const uint32_t bytes = (uint32_t)nbulk * (uint32_t)sizeof(cf);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(f32_saddr(bb)), "r"(bytes)
+                 : "memory");
+    if (nbulk > 0)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              f32_saddr(view + head)),
+          "l"(src + head), "r"(bytes), "r"(f32_saddr(bb))
+          : "memory");
+  };
+  cf c_next = make_float2(0.f, 0.f), y_next = make_float2(0.f, 0.f);
+  cd f_next = make_double2(0, 0), ta_next = make_double2(0, 0), tb_next = make_double2(0, 0);
+  auto prefetch = [&](int st) {
+    if (!own) return;
+    const int i = col(st);
+    const bool fwd = st < nt;
+    c_next = __ldg((fwd ? Whi : Ehi) + L.coef_off + (size_t)i * n + r);
+    if (fwd) {
+      cd v = make_double2(0, 0);
+      if (fnz && in_layer) v = fs[frow + i];
+      f_next = v;
+      if (MODE == 1 && ftr >= 0) {
+        ta_next = xs[(size_t)ftr * nt + i];
+        tb_next = xs[(size_t)(T + ftr) * nt + i];
+      }
+    } else {
+      y_next = Y[(size_t)i * n + r];
+    }
+  };
+
+  cf chain = make_float2(0.f, 0.f);
+  // after a timed-out wait the CTA stops computing but keeps taking part in every
+  // cluster barrier, so its peers are never left waiting; the error is in *status
+  bool alive = true;
+  __syncthreads();  // mbarriers initialised
+  stage(0);
+  prefetch(0);
+  cluster.sync();  // every CTA of the cluster is resident before remote stores
+  for (int st = 0; st < nsteps; ++st) {
+    const bool fwd = st < nt;
+    const int i = col(st);
+    cf* vb = vbuf + (st & 1) * kMaxNloc;
+    // (a) right-hand side of my rows, broadcast to every CTA of the cluster
+    if (own) {
+      const cf c = c_next;
+      float vr, vi;
+      if (fwd) {
+        cd d = f_next;
+        if (MODE == 1 && ftr >= 0) d = cadd(d, cscale(cadd(ta_next, tb_next), (double)fsg));
+        vr = (float)d.x;
+        vi = (float)d.y;
+        if (i > 0) {
+          vr -= c.x * chain.x - c.y * chain.y;
+          vi -= c.x * chain.y + c.y * chain.x;
+        }
+      } else {
+        vr = c.x * chain.x - c.y * chain.y;
+        vi = c.x * chain.y + c.y * chain.x;
+      }
+      const cf v = make_float2(vr, vi);
+#pragma unroll
+      for (int p = 0; p < CS; ++p) cluster.map_shared_rank(vb, p)[r] = v;
+    }
+    const cf yst = y_next;
+    cluster.sync();  // v complete in every CTA; this CTA's reads of step st - 1 are over
+    if (alive && st + 1 < nsteps) {
+      stage(st + 1);     // the other buffer was last read in step st - 1
+      prefetch(st + 1);  // consumed before the next barrier
+    }
+    if (alive) alive = __all_sync(0xffffffffu, f32_mb_wait(&bar[st & 1], (st >> 1) & 1, status));
+    if (!alive) continue;
+    // (b) my rows of Sinv_i v
+    const cf* Srow = view_of(st) + (size_t)min(lr, max(r1 - r0 - 1, 0)) * n;
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      const cf a0 = Srow[k], a1 = Srow[k + 1];
+      const cf v0 = vb[k], v1 = vb[k + 1];
+      ar = fmaf(a0.x, v0.x, ar); ar = fmaf(-a0.y, v0.y, ar);
+      ai = fmaf(a0.x, v0.y, ai); ai = fmaf(a0.y, v0.x, ai);
+      br = fmaf(a1.x, v1.x, br); br = fmaf(-a1.y, v1.y, br);
+      bi = fmaf(a1.x, v1.y, bi); bi = fmaf(a1.y, v1.x, bi);
+    }
+    if (k < k1) {
+      const cf a0 = Srow[k], v0 = vb[k];
+      ar = fmaf(a0.x, v0.x, ar); ar = fmaf(-a0.y, v0.y, ar);
+      ai = fmaf(a0.x, v0.y, ai); ai = fmaf(a0.y, v0.x, ai);
+    }
+    ar += br;
+    ai += bi;
+#pragma unroll
+    for (int o = 1; o < kF32cQ; o <<= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (own) {
+      if (fwd) {
+        chain = make_float2(ar, ai);
+        Y[(size_t)i * n + r] = chain;
+      } else {
+        chain = make_float2(yst.x - ar, yst.y - ai);
+      }
+      if (!fwd || i == nt - 1) {
+        if (MODE == 0) {
+          if (emit >= 0) out[(size_t)s * T4n + (size_t)emit * nt + i] = make_double2(-(double)chain.x, -(double)chain.y);
+        } else if (in_layer) {
+          out[(size_t)s * g.Nz * nt + frow + i] = make_double2((double)chain.x, (double)chain.y);
+        }
+      }
+    }
+  }
+  cluster.sync();  // no CTA leaves while a peer may still write its shared memory
+}
+
+// FP32 single-source local solves: cluster = 4 or 8 CTAs per (layer, source), else one CTA
 cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo* layers, int nloc_max, const cf* Shi,
                                    const cf* Whi, const cf* Ehi, const cd* f, const cd* xtr, cd* Y, size_t ystride,
-                                   cd* out, const int* flag, int nsrc, int* status, cudaStream_t s) {
+                                   cd* out, const int* flag, int nsrc, int* status, int cluster, cudaStream_t s) {
   if (nloc_max < 1 || nloc_max > kMaxNloc || nloc_max * kF32Q > kF32Threads) return cudaErrorInvalidValue;
-  const size_t smem = f32_solve_smem(nloc_max);
   cf* Yc = reinterpret_cast<cf*>(Y);
-  dim3 grid(g.L, nsrc);
   cudaError_t e;
+  if (cluster == 4 || cluster == 8) {
+    static_assert(F32cLayout<4>::RPC * kF32cQ <= kF32cThreads, "rows x threads per row");
+    auto go = [&](auto kern, int CS, size_t smem) {
+      cudaError_t err = smem_limit_max(reinterpret_cast<const void*>(kern));
+      if (err != cudaSuccess) return err;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(CS * g.L, nsrc);
+      cfg.blockDim = dim3(kF32cThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, kern, g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag, status);
+    };
+    if (cluster == 4)
+      e = mode == 0 ? go(layer_solve_f32c_kernel<0, 4>, 4, F32cLayout<4>::bytes)
+                    : go(layer_solve_f32c_kernel<1, 4>, 4, F32cLayout<4>::bytes);
+    else
+      e = mode == 0 ? go(layer_solve_f32c_kernel<0, 8>, 8, F32cLayout<8>::bytes)
+                    : go(layer_solve_f32c_kernel<1, 8>, 8, F32cLayout<8>::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  const size_t smem = f32_solve_smem(nloc_max);
+  dim3 grid(g.L, nsrc);
   if (mode == 0) {
     e = smem_limit_max(reinterpret_cast<const void*>(layer_solve_f32_kernel<0>));
     if (e != cudaSuccess) return e;

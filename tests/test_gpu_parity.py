@@ -120,9 +120,9 @@ def test_mixed_fp32_preconditioner_meets_mixed_tolerance(small):
     assert _rel(u.cpu().numpy()[0], u_ref) < 1e-5
 
 
-@pytest.mark.parametrize("variant,tol_field", [(0, 1e-5), (1, 1e-8)])
+@pytest.mark.parametrize("variant,tol_field", [(0, 1e-5), (1, 1e-8), (2, 1e-5), (3, 1e-5)])
 def test_mixed_local_solve_variants_match_oracle(small, variant, tol_field):
-    """FP32 single-CTA local solves (default) and double-float cluster ones, on a point
+    """FP32 local solves on clusters of 4 (default) or 8 CTAs or on one CTA, and double-float ones, on a point
     source and on a source that excites every layer."""
     from paper_1410_5910_gb300 import PT_OPT_LOCAL_SOLVE
 
