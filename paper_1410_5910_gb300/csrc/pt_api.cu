@@ -35,7 +35,7 @@ cudaError_t launch_apply_mode(int, int, int, int, const ApplyRow*, int, const vo
                               const cd*, cd*, int, int, double, double, cudaStream_t);
 cudaError_t launch_split_blocks(const cd*, int, int, size_t, cf*, cf*, cudaStream_t);
 cudaError_t launch_split_sinv(const cd*, size_t, cf*, cf*, cudaStream_t);
-cudaError_t launch_layer_nonzero(const Geometry&, const LayerInfo*, const cd*, int*, int, cudaStream_t);
+cudaError_t launch_layer_nonzero(const Geometry&, const LayerInfo*, const cd*, int*, int*, int, cudaStream_t);
 cudaError_t launch_layer_solve(int, const Geometry&, const LayerInfo*, const cd*, const cd*, const cd*, const cd*,
                                const cd*, cd*, size_t, cd*, const int*, int, cudaStream_t);
 cudaError_t launch_layer_solve2(int, bool, const Geometry&, const LayerInfo*, const cd*, const cf*, const cf*,
@@ -64,7 +64,8 @@ cudaError_t launch_tc_apply(int, const CUtensorMap&, const CUtensorMap&, const C
                             const TcRow*, int, int, int, int, int, const float*, const cd*, const cd*, cd*, double,
                             double, int*, cudaStream_t);
 cudaError_t launch_layer_solve_f32(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
-                                   const cd*, const cd*, cd*, size_t, cd*, const int*, int, int*, int, cudaStream_t);
+                                   const cd*, const cd*, cd*, size_t, cd*, const int*, const int*, int, int*, int,
+                                   cudaStream_t);
 cudaError_t launch_layer_solve_batch(int, const Geometry&, const LayerInfo*, int, const cf*, const cf*, const cf*,
                                      const cd*, const cd*, cd*, cd*, const int*, int, int, cudaStream_t);
 cudaError_t nn_forward(const __nv_bfloat16*, const float*, const float*, long, int, float*, float*, float*,
@@ -380,6 +381,7 @@ size_t plr_setup_bytes(const Plan& P) {
 struct SolveBufs {
   cd* Y;
   int* nzflag;
+  int* nzfirst;  // first grid column of f^l with a non-zero entry
   cd *b, *x, *w, *t, *u1, *V, *Z, *partial, *coef, *H, *sn, *g, *y;
   double *cs, *resid, *nrm;
   int* kk;
@@ -401,6 +403,7 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
   // round_up(S, 32) sources in half the bytes
   b.Y = c.take<cd>((size_t)(P.tc ? std::max(S, 16) : S) * P.L * P.nt * P.nloc_max);
   b.nzflag = c.take<int>((size_t)S * P.L);
+  b.nzfirst = c.take<int>((size_t)S * P.L);
   b.b = c.take<cd>(S * N);
   b.x = c.take<cd>(S * N);
   b.w = c.take<cd>(S * N);
@@ -1036,7 +1039,7 @@ cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xt
     if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
     if (c->opt_local_solve != 1)  // FP32 on a cluster of 4 (0) or 8 (3) CTAs, or one CTA (2), per (layer, source)
       return launch_layer_solve_f32(mode, P.g, c->d.layers, P.nloc_max, c->d.sinv_hi, c->d.w_hi, c->d.e_hi, f, xtr,
-                                    B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->d.status,
+                                    B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, B.nzfirst, S, c->d.status,
                                     c->opt_local_solve == 0 ? 4 : (c->opt_local_solve == 3 ? 8 : 1), c->stream);
     return launch_layer_solve_df(mode, P.g, c->d.layers, c->d.sinv_hi, c->d.sinv_lo, c->d.w_hi, c->d.w_lo, c->d.e_hi,
                                  c->d.e_lo, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, S, c->stream);
@@ -1047,7 +1050,7 @@ cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xt
 
 cudaError_t do_rhs(pt_ctx* c, int S, const cd* f, cd* b, const SolveBufs& B) {
   c->launches++;
-  cudaError_t e = launch_layer_nonzero(c->P.g, c->d.layers, f, B.nzflag, S, c->stream);
+  cudaError_t e = launch_layer_nonzero(c->P.g, c->d.layers, f, B.nzflag, B.nzfirst, S, c->stream);
   if (e != cudaSuccess) return e;
   return do_layer_solve(c, 0, S, f, nullptr, b, B);
 }
@@ -1473,7 +1476,7 @@ extern "C" pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128
   if (st != PT_OK) return st;
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
   const cd* fd = reinterpret_cast<const cd*>(f);
-  PT_CUDA(launch_layer_nonzero(ctx->P.g, ctx->d.layers, fd, B.nzflag, nsrc, ctx->stream));
+  PT_CUDA(launch_layer_nonzero(ctx->P.g, ctx->d.layers, fd, B.nzflag, nullptr, nsrc, ctx->stream));
   PT_CUDA(launch_layer_solve(0, ctx->P.g, ctx->d.layers, ctx->d.Sinv, ctx->d.W, ctx->d.E, fd, nullptr, B.Y,
                              (size_t)ctx->P.nt * ctx->P.nloc_max, reinterpret_cast<cd*>(y), B.nzflag, nsrc,
                              ctx->stream));
@@ -1764,7 +1767,7 @@ extern "C" pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f,
   cd* Y = static_cast<cd*>(base);
   int* flag = reinterpret_cast<int*>(static_cast<char*>(base) + ybytes);
   const cd* fd = reinterpret_cast<const cd*>(f);
-  PT_CUDA(launch_layer_nonzero(P.g, ctx->d.layers, fd, flag, nsrc, ctx->stream));
+  PT_CUDA(launch_layer_nonzero(P.g, ctx->d.layers, fd, flag, nullptr, nsrc, ctx->stream));
   PT_CUDA(launch_layer_solve(0, P.g, ctx->d.layers, ctx->d.Sinv, ctx->d.W, ctx->d.E, fd, nullptr, Y, ystride,
                              reinterpret_cast<cd*>(y), flag, nsrc, ctx->stream));
   PT_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -766,7 +766,8 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
     layer_solve_f32c_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cf* __restrict__ Shi,
                             const cf* __restrict__ Whi, const cf* __restrict__ Ehi, const cd* __restrict__ f,
                             const cd* __restrict__ xtr, cf* __restrict__ Ystore, size_t ystride,
-                            cd* __restrict__ out, const int* __restrict__ nzflag, int* __restrict__ status) {
+                            cd* __restrict__ out, const int* __restrict__ nzflag, const int* __restrict__ firstcol,
+                            int* __restrict__ status) {
   using Lay = F32cLayout<CS>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -809,6 +810,9 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
   cf* Y = Ystore + ((size_t)s * g.L + l) * ystride;
   const int nsteps = 2 * nt - 1;
   auto col = [&](int st) { return st < nt ? st : nt - 2 - (st - nt); };
+  // right-hand side of point sources: the forward iterates vanish before the first column
+  // with a non-zero source entry, so the chain starts there (stored iterates read as zero)
+  const int st0 = (MODE == 0 && firstcol) ? min(firstcol[s * g.L + l], nt - 1) : 0;
   const bool in_layer = own && r >= L.pad_top && r < L.pad_top + L.n;
   const size_t frow = in_layer ? (size_t)(L.start + r - L.pad_top) * nt : 0;
   int ftr = -1;
@@ -830,7 +834,7 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
   const int cnt = (r1 - r0) * n;  // this CTA's slice of a column: contiguous rows r0 .. r1 - 1
   auto src_of = [&](int st) { return Shi + L.sinv_off + (size_t)col(st) * n * n + (size_t)r0 * n; };
   auto view_of = [&](int st) {
-    cf* B = (st & 1) ? B1 : B0;
+    cf* B = ((st - st0) & 1) ? B1 : B0;
     return ((reinterpret_cast<uintptr_t>(src_of(st)) & 15) != 0) ? B + 1 : B;
   };
   if (threadIdx.x == 0) {
@@ -848,7 +852,7 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
     const int nbulk = m & ~1;
     if (head) view[0] = src[0];
     if (m & 1) view[cnt - 1] = src[cnt - 1];
-    uint64_t* bb = &bar[st & 1];
+    uint64_t* bb = &bar[(st - st0) & 1];
     const uint32_t bytes = (uint32_t)nbulk * (uint32_t)sizeof(cf);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(f32_saddr(bb)), "r"(bytes)
@@ -876,7 +880,9 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
         tb_next = xs[(size_t)(T + ftr) * nt + i];
       }
     } else {
-      y_next = Y[(size_t)i * n + r];
+      cf y = make_float2(0.f, 0.f);
+      if (i >= st0) y = Y[(size_t)i * n + r];
+      y_next = y;
     }
   };
 
@@ -885,13 +891,14 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
   // cluster barrier, so its peers are never left waiting; the error is in *status
   bool alive = true;
   __syncthreads();  // mbarriers initialised
-  stage(0);
-  prefetch(0);
+  stage(st0);
+  prefetch(st0);
   cluster.sync();  // every CTA of the cluster is resident before remote stores
-  for (int st = 0; st < nsteps; ++st) {
+  for (int st = st0; st < nsteps; ++st) {
     const bool fwd = st < nt;
     const int i = col(st);
-    cf* vb = vbuf + (st & 1) * kMaxNloc;
+    const int t = st - st0;  // local step: buffer and barrier-phase parity
+    cf* vb = vbuf + (t & 1) * kMaxNloc;
     // (a) right-hand side of my rows, broadcast to every CTA of the cluster
     if (own) {
       const cf c = c_next;
@@ -919,7 +926,7 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
       stage(st + 1);     // the other buffer was last read in step st - 1
       prefetch(st + 1);  // consumed before the next barrier
     }
-    if (alive) alive = __all_sync(0xffffffffu, f32_mb_wait(&bar[st & 1], (st >> 1) & 1, status));
+    if (alive) alive = __all_sync(0xffffffffu, f32_mb_wait(&bar[t & 1], (t >> 1) & 1, status));
     if (!alive) continue;
     // (b) my rows of Sinv_i v
     const cf* Srow = view_of(st) + (size_t)min(lr, max(r1 - r0 - 1, 0)) * n;
@@ -967,7 +974,8 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
 // FP32 single-source local solves: cluster = 4 or 8 CTAs per (layer, source), else one CTA
 cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo* layers, int nloc_max, const cf* Shi,
                                    const cf* Whi, const cf* Ehi, const cd* f, const cd* xtr, cd* Y, size_t ystride,
-                                   cd* out, const int* flag, int nsrc, int* status, int cluster, cudaStream_t s) {
+                                   cd* out, const int* flag, const int* firstcol, int nsrc, int* status, int cluster,
+                                   cudaStream_t s) {
   if (nloc_max < 1 || nloc_max > kMaxNloc || nloc_max * kF32Q > kF32Threads) return cudaErrorInvalidValue;
   cf* Yc = reinterpret_cast<cf*>(Y);
   cudaError_t e;
@@ -988,7 +996,8 @@ cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo*
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      return cudaLaunchKernelEx(&cfg, kern, g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag, status);
+      return cudaLaunchKernelEx(&cfg, kern, g, layers, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag, firstcol,
+                                status);
     };
     if (cluster == 4)
       e = mode == 0 ? go(layer_solve_f32c_kernel<0, 4>, 4, F32cLayout<4>::bytes)
@@ -1015,19 +1024,31 @@ cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo*
   return cudaGetLastError();
 }
 
-// flag[s * L + l] = 1 when f^l of source s has a non-zero entry
+// flag[s * L + l] = 1 when f^l of source s has a non-zero entry; first (optional) = the
+// first grid column with one (n_t when none): the forward substitution is zero before it
 __global__ void layer_nonzero_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cd* __restrict__ f,
-                                     int* __restrict__ flag) {
+                                     int* __restrict__ flag, int* __restrict__ first) {
   const LayerInfo L = layers[blockIdx.x];
   const int s = blockIdx.y;
   const cd* fs = f + (size_t)s * g.Nz * g.nt + (size_t)L.start * g.nt;
-  int nz = 0;
+  int nz = 0, fc = g.nt;
   for (size_t k = threadIdx.x; k < (size_t)L.n * g.nt; k += blockDim.x) {
     cd v = fs[k];
-    nz |= (v.x != 0.0 || v.y != 0.0);
+    if (v.x != 0.0 || v.y != 0.0) {
+      nz = 1;
+      fc = min(fc, (int)(k % g.nt));
+    }
   }
   nz = __syncthreads_or(nz);
-  if (threadIdx.x == 0) flag[s * g.L + blockIdx.x] = nz;
+  __shared__ int smin;
+  if (threadIdx.x == 0) smin = g.nt;
+  __syncthreads();
+  if (fc < g.nt) atomicMin(&smin, fc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    flag[s * g.L + blockIdx.x] = nz;
+    if (first) first[s * g.L + blockIdx.x] = smin;
+  }
 }
 
 __global__ void split_sinv_kernel(const cd* __restrict__ src, size_t n, cf* __restrict__ hi, cf* __restrict__ lo) {
@@ -1039,9 +1060,9 @@ __global__ void split_sinv_kernel(const cd* __restrict__ src, size_t n, cf* __re
   }
 }
 
-cudaError_t launch_layer_nonzero(const Geometry& g, const LayerInfo* layers, const cd* f, int* flag, int nsrc,
-                                 cudaStream_t s) {
-  layer_nonzero_kernel<<<dim3(g.L, nsrc), 256, 0, s>>>(g, layers, f, flag);
+cudaError_t launch_layer_nonzero(const Geometry& g, const LayerInfo* layers, const cd* f, int* flag, int* first,
+                                 int nsrc, cudaStream_t s) {
+  layer_nonzero_kernel<<<dim3(g.L, nsrc), 256, 0, s>>>(g, layers, f, flag, first);
   return cudaGetLastError();
 }
 
