@@ -490,11 +490,11 @@ def main():
         ystore = sum(2 * nt * n_ * 8 for n_ in nloc)
         vol = wl.Nz * nt * 16 + 4 * (L_ - 1) * nt * 16
         alg = (sinv + coef + ystore + vol) * S
-        # DRAM traffic of the same kernel on the 255 x 511, L = 8 layered case (ncu): 0.79 x its
+        # DRAM traffic of the same kernel on the 255 x 511, L = 8 layered case (ncu): 0.80 x its
         # algorithmic bytes (L2 serves the columns around the forward / backward turn); traffic grows
         # with the units (column steps x rows^2), so it is scaled
-        traffic = 0.79 * alg
-        roof = {"kernel": "layer_solve_f32_kernel<1> (FP32 local solves, reconstruction of every layer)",
+        traffic = 0.80 * alg
+        roof = {"kernel": "layer_solve_f32c_kernel<1, 4> (FP32 local solves on 4-CTA clusters, reconstruction)",
                 "bound": "hbm", "achieved": alg / t_launch / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": traffic, "algorithmic_bytes": alg, "launch_ms": t_launch * 1e3,
                 "latency_bound": f"{steps} dependent column steps, {t_launch / steps * 1e6:.2f} us per step",

@@ -887,6 +887,23 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
   };
 
   cf chain = make_float2(0.f, 0.f);
+  // Global stores of a step (the stored forward iterate, the output) are issued after the
+  // next step's cluster barrier, so that barrier's release does not wait for them
+  int pend_i = -1;
+  bool pend_fwd = false;
+  auto flush = [&]() {
+    if (!own || pend_i < 0) return;
+    const int i = pend_i;
+    if (pend_fwd) Y[(size_t)i * n + r] = chain;
+    if (!pend_fwd || i == nt - 1) {
+      if (MODE == 0) {
+        if (emit >= 0) out[(size_t)s * T4n + (size_t)emit * nt + i] = make_double2(-(double)chain.x, -(double)chain.y);
+      } else if (in_layer) {
+        out[(size_t)s * g.Nz * nt + frow + i] = make_double2((double)chain.x, (double)chain.y);
+      }
+    }
+    pend_i = -1;
+  };
   // after a timed-out wait the CTA stops computing but keeps taking part in every
   // cluster barrier, so its peers are never left waiting; the error is in *status
   bool alive = true;
@@ -922,6 +939,7 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
     }
     const cf yst = y_next;
     cluster.sync();  // v complete in every CTA; this CTA's reads of step st - 1 are over
+    flush();         // the previous step's global stores
     if (alive && st + 1 < nsteps) {
       stage(st + 1);     // the other buffer was last read in step st - 1
       prefetch(st + 1);  // consumed before the next barrier
@@ -953,21 +971,12 @@ __global__ void __launch_bounds__(kF32cThreads, 1)
       ai += __shfl_xor_sync(0xffffffffu, ai, o);
     }
     if (own) {
-      if (fwd) {
-        chain = make_float2(ar, ai);
-        Y[(size_t)i * n + r] = chain;
-      } else {
-        chain = make_float2(yst.x - ar, yst.y - ai);
-      }
-      if (!fwd || i == nt - 1) {
-        if (MODE == 0) {
-          if (emit >= 0) out[(size_t)s * T4n + (size_t)emit * nt + i] = make_double2(-(double)chain.x, -(double)chain.y);
-        } else if (in_layer) {
-          out[(size_t)s * g.Nz * nt + frow + i] = make_double2((double)chain.x, (double)chain.y);
-        }
-      }
+      chain = fwd ? make_float2(ar, ai) : make_float2(yst.x - ar, yst.y - ai);
+      pend_i = i;
+      pend_fwd = fwd;
     }
   }
+  flush();
   cluster.sync();  // no CTA leaves while a peer may still write its shared memory
 }
 
