@@ -81,6 +81,8 @@ cudaError_t nn_gather(const float*, long, const int*, int, int, int, float*, cud
 cudaError_t nn_sub(const cd*, const cd*, cd*, size_t, cudaStream_t);
 cudaError_t nn_sumsq(const float*, long, double*, cudaStream_t);
 cudaError_t nn_scale(float*, long, float, cudaStream_t);
+bool launch_apply_f32_rows(int, int, int, const ApplyRow*, int, const void*, const cd*, const cd*, cd*, int, double,
+                           double, cudaStream_t, cudaError_t*);
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
@@ -628,6 +630,7 @@ struct pt_ctx {
   __half *tc_bhi = nullptr, *tc_blo = nullptr;
   float *tc_scale = nullptr, *tc_inv = nullptr;
   int opt_layer_group = 0;  // PT_OPT_LAYER_GROUP
+  int sweep_terms_max = 0;  // block terms of the longest sweep row
   int opt_local_solve = 0;  // PT_OPT_LOCAL_SOLVE
   // learned correction
   bool nn_ready = false;    // weights set or trained
@@ -835,6 +838,8 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
     return bail(fail(PT_ERR_CUDA, "copying tables"));
   TableBuilder tb{P};
   auto mv = tb.matvec(), rr = tb.coupling(), sw = tb.sweeps();
+  c->sweep_terms_max = 0;
+  for (const ApplyRow& ar : sw) c->sweep_terms_max = std::max(c->sweep_terms_max, ar.nterms);
   if (cudaMemcpyAsync(c->d.tab_matvec, mv.data(), mv.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(c->d.tab_R, rr.data(), rr.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(c->d.tab_sweep, sw.data(), sw.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -943,6 +948,13 @@ cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, cons
   if (mode == kModeFP64)
     return launch_apply_mode(kModeFP64, P.nt, P.nt, P.T4, op.table, op.nrows, c->d.blocks, nullptr, x, aux, y, S,
                              rows_per_cta, alpha, beta, c->stream);
+  if (mode == kModeFP32 && rows_per_cta == kApplyRowsSweep && c->sweep_terms_max <= 2) {
+    // sweep steps: one row per warp with both block rows in flight
+    cudaError_t e = cudaSuccess;
+    if (launch_apply_f32_rows(P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, x, aux, y, S, alpha, beta,
+                              c->stream, &e))
+      return e;
+  }
   return launch_apply_mode(mode, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, c->d.blocks_lo, x, aux, y,
                            S, rows_per_cta, alpha, beta, c->stream);
 }

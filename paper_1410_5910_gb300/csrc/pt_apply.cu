@@ -230,6 +230,118 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
   }
 }
 
+// ---- FP32 sweep steps: one row per warp, whole block rows in flight ---------------
+// A sweep step (Section 4.1) is small (8 blocks): the time is memory latency, not
+// bandwidth.  Each lane issues the loads of its share of both terms' block rows into
+// registers first (up to MAXC float4 = 2 complex64 each per term), then the CTA stages
+// the input traces, so the two latencies overlap and a row costs one round trip.
+template <int MAXC>
+__global__ void __launch_bounds__(256) apply_f32_rows_kernel(int nt, int ld, int T4, const ApplyRow* __restrict__ table,
+                                                             const cf* __restrict__ blocks, const cd* x,
+                                                             const cd* __restrict__ aux, cd* y, double alpha,
+                                                             double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ApplyRow row;
+  if (threadIdx.x == 0) row = table[blockIdx.z];
+  __syncthreads();
+  const int s = blockIdx.x;
+  const size_t vs = (size_t)T4 * nt;
+  const cd* xs = x + s * vs;
+  const cd* as = aux ? aux + s * vs : nullptr;
+  const size_t bsz = (size_t)nt * ld;
+  const int nterms = row.nterms;  // <= 2 (checked by the launcher's table)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.y * 8 + warp;
+  const int np = ld >> 1;
+  // (1) this warp's block rows, all loads in flight
+  float4 b[2][MAXC];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float4* B = (t < nterms && r < nt)
+                          ? reinterpret_cast<const float4*>(blocks + (size_t)row.t[t].block * bsz + (size_t)r * ld)
+                          : nullptr;
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      const int k = lane + 32 * c;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (B && k < np) v = __ldg(B + k);
+      b[t][c] = v;
+    }
+  }
+  // (2) sign_t (x[in1] + x[in2]) as complex64, padded with zeros to ld
+  cf* xin = reinterpret_cast<cf*>(smem_raw);
+  for (int t = 0; t < nterms; ++t) {
+    const ApplyTerm tm = row.t[t];
+    const cd* a = xs + (size_t)tm.in1 * nt;
+    const cd* bb = tm.in2 >= 0 ? xs + (size_t)tm.in2 * nt : nullptr;
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+      cd v = make_double2(0, 0);
+      if (k < nt) {
+        v = a[k];
+        if (bb) v = cadd(v, bb[k]);
+        v = cscale(v, tm.sign);
+      }
+      xin[t * ld + k] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+  __syncthreads();
+  if (r >= nt) return;
+  // (3) products
+  float are = 0.f, aim = 0.f;
+  const float4* xv4 = reinterpret_cast<const float4*>(xin);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    if (t >= nterms) break;
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      const int k = lane + 32 * c;
+      if (k < np) {
+        const float4 v = xv4[t * np + k], bv = b[t][c];
+        are = fmaf(bv.x, v.x, are);
+        are = fmaf(-bv.y, v.y, are);
+        are = fmaf(bv.z, v.z, are);
+        are = fmaf(-bv.w, v.w, are);
+        aim = fmaf(bv.x, v.y, aim);
+        aim = fmaf(bv.y, v.x, aim);
+        aim = fmaf(bv.z, v.w, aim);
+        aim = fmaf(bv.w, v.z, aim);
+      }
+    }
+  }
+  const cf acc = warp_sum_cf(make_float2(are, aim));
+  if (lane == 0) {
+    cd val = make_double2(acc.x, acc.y);
+    for (int e = 0; e < row.nid; ++e) {
+      const cd* src = row.id_src[e] == 0 ? xs : as;
+      val = cadd(val, cscale(src[(size_t)row.id_trace[e] * nt + r], row.id_sign[e]));
+    }
+    val = cscale(val, alpha);
+    if (beta != 0.0) val = cadd(val, cscale(as[(size_t)row.out * nt + r], beta));
+    y[s * vs + (size_t)row.out * nt + r] = val;
+  }
+}
+
+// FP32 rows of at most two terms, 8 rows per CTA; false when the row length exceeds the register bound
+bool launch_apply_f32_rows(int nt, int ld, int T4, const ApplyRow* table, int nrows, const void* blocks, const cd* x,
+                           const cd* aux, cd* y, int nsrc, double alpha, double beta, cudaStream_t s,
+                           cudaError_t* err) {
+  const int np = ld >> 1;
+  const size_t smem = 2ull * ld * sizeof(cf);
+  dim3 grid(nsrc, (nt + 7) / 8, nrows);
+  const cf* B = static_cast<const cf*>(blocks);
+  if (np <= 32 * 4) {
+    apply_f32_rows_kernel<4><<<grid, 256, smem, s>>>(nt, ld, T4, table, B, x, aux, y, alpha, beta);
+  } else if (np <= 32 * 9) {
+    apply_f32_rows_kernel<9><<<grid, 256, smem, s>>>(nt, ld, T4, table, B, x, aux, y, alpha, beta);
+  } else if (np <= 32 * 18) {
+    apply_f32_rows_kernel<18><<<grid, 256, smem, s>>>(nt, ld, T4, table, B, x, aux, y, alpha, beta);
+  } else {
+    return false;
+  }
+  *err = cudaGetLastError();
+  return true;
+}
+
 // ---- conversion of FP64 blocks to the FP32 / double-float layouts -----------
 // hi[b][r][k] = fl32(src), lo = fl32(src - hi), rows padded from nt to ld with zeros.
 __global__ void split_blocks_kernel(const cd* __restrict__ src, int nt, int ld, size_t nrows_total,
