@@ -68,8 +68,10 @@ typedef enum {
                         ~1e-14); local solves (right-hand side, reconstruction) in
                         FP32 with the FP64 factors rounded to complex64 (~1e-6 on
                         the field; PT_OPT_LOCAL_SOLVE = 1 selects double-float);
-                        Arnoldi, least squares and the explicit residual in FP64
-                        (flexible GMRES)                                            */
+                        the explicit residual between restart cycles in double-float;
+                        Arnoldi and least squares in FP64 (flexible GMRES).  With
+                        compressed blocks (plr) the products are FP64 instead of
+                        double-float.                                               */
   PT_MIXED_TC = 2    /* for batches of sources: the block products run on the tensor
                         cores with FP16 operands (power-of-two scales) and FP32
                         accumulation - one pass in the preconditioner, the three-pass
@@ -241,8 +243,13 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * the next column's factors in shared memory (default, ~1e-6 on the field);
  * 3 = the same on 8 CTAs; 2 = FP32 on one CTA; 1 = double-float on clusters
  * of 4 CTAs (~1e-13, slower).
+ * PT_OPT_SWEEP: the sweeps D^{-1} of the PT_MIXED_FP32 preconditioner -
+ * 0 = all L-1 steps of a sweep in one cooperative launch with a grid barrier
+ * between steps (default; used when the shape fits its register and shared-
+ * memory bounds, and never inside pt_solve_many, whose contexts share the
+ * GPU); 1 = one launch per step.  Both give the same products.
  * PT_ERR_ARG for an unknown option or value. */
-enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3 };
+enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3, PT_OPT_SWEEP = 4 };
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
 
 /* ---- learned preconditioner correction (not in the paper) ------------------

@@ -29,6 +29,7 @@ EXPORTS = [
 PT_OPT_LAYER_GROUP = 1
 PT_OPT_LEARNED = 2
 PT_OPT_LOCAL_SOLVE = 3
+PT_OPT_SWEEP = 4
 
 
 class Params(C.Structure):

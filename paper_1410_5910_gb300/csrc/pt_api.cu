@@ -83,6 +83,8 @@ cudaError_t nn_sumsq(const float*, long, double*, cudaStream_t);
 cudaError_t nn_scale(float*, long, float, cudaStream_t);
 bool launch_apply_f32_rows(int, int, int, const ApplyRow*, int, const void*, const cd*, const cd*, cd*, int, double,
                            double, cudaStream_t, cudaError_t*);
+bool launch_sweep_f32(int, int, int, int, const ApplyRow*, const void*, const cd*, cd*, cf*, int, unsigned*, int*,
+                      cudaStream_t, cudaError_t*);
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
@@ -97,6 +99,8 @@ cudaError_t launch_sub(const cd*, const cd*, cd*, size_t, cudaStream_t);
 using namespace pt;
 
 static thread_local std::string g_last_error;
+// set on the worker threads of pt_solve_many: contexts that share the GPU take no cooperative launches
+static thread_local bool g_shared_gpu = false;
 
 static pt_status fail(pt_status s, const std::string& msg) {
   g_last_error = msg;
@@ -250,6 +254,8 @@ pt_status make_plan(const pt_params* p, Plan& P) {
 struct Persist {
   LayerInfo* layers;
   int* status;
+  unsigned* sweep_bar;  // grid-barrier counter of the one-launch sweeps
+  cf* sweep_y32;        // complex64 copies of the traces a one-launch sweep writes (mixed FP32 form)
   cd* W;
   cd* E;
   cd* Sinv;
@@ -300,6 +306,7 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
   Persist q{};
   q.layers = c.take<LayerInfo>(P.L);
   q.status = c.take<int>(64);
+  q.sweep_bar = c.take<unsigned>(64);
   q.W = c.take<cd>(P.coef_elems);
   q.E = c.take<cd>(P.coef_elems);
   q.Sinv = c.take<cd>(P.sinv_elems);
@@ -318,6 +325,7 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
     q.e_hi = c.take<cf>(P.coef_elems);
     q.e_lo = c.take<cf>(P.coef_elems);
   }
+  if (p->precision == PT_MIXED_FP32 && !P.plr) q.sweep_y32 = c.take<cf>((size_t)p->max_sources * P.T4 * P.nt);
   q.tab_matvec = c.take<ApplyRow>(P.T4);
   q.tab_R = c.take<ApplyRow>(P.T4);
   q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
@@ -584,6 +592,28 @@ void tc_from(const ApplyRow* rows, int nrows, int nt, std::vector<TcRow>& out, s
   }
 }
 
+// The one-launch FP32 sweep stages one input per (pair of output traces, term): rows 2g and
+// 2g+1 of every step must have the same terms up to their blocks, single input traces and
+// identities on the auxiliary vector.
+bool sweep_pairs_match(const std::vector<ApplyRow>& sw) {
+  if (sw.size() % 4 != 0) return false;
+  for (size_t i = 0; i < sw.size(); ++i) {
+    const ApplyRow& a = sw[i];
+    if (a.nterms > 2) return false;
+    for (int t = 0; t < a.nterms; ++t)
+      if (a.t[t].in2 >= 0) return false;
+    for (int e = 0; e < a.nid; ++e)
+      if (a.id_src[e] != 1) return false;
+    if (i % 2 == 1) {
+      const ApplyRow& b = sw[i - 1];
+      if (a.nterms != b.nterms) return false;
+      for (int t = 0; t < a.nterms; ++t)
+        if (a.t[t].in1 != b.t[t].in1 || a.t[t].sign != b.t[t].sign) return false;
+    }
+  }
+  return true;
+}
+
 pt_status full_plan(const pt_params* p, Plan& P) {
   pt_status st = make_plan(p, P);
   if (st != PT_OK) return st;
@@ -632,6 +662,8 @@ struct pt_ctx {
   int opt_layer_group = 0;  // PT_OPT_LAYER_GROUP
   int sweep_terms_max = 0;  // block terms of the longest sweep row
   int opt_local_solve = 0;  // PT_OPT_LOCAL_SOLVE
+  int opt_sweep = 0;        // PT_OPT_SWEEP
+  bool sweep_fusable = false;  // sweep tables have the pair layout of the one-launch sweep
   // learned correction
   bool nn_ready = false;    // weights set or trained
   int nn_t = 0;             // Adam steps taken
@@ -840,6 +872,7 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   auto mv = tb.matvec(), rr = tb.coupling(), sw = tb.sweeps();
   c->sweep_terms_max = 0;
   for (const ApplyRow& ar : sw) c->sweep_terms_max = std::max(c->sweep_terms_max, ar.nterms);
+  c->sweep_fusable = sweep_pairs_match(sw);
   if (cudaMemcpyAsync(c->d.tab_matvec, mv.data(), mv.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(c->d.tab_R, rr.data(), rr.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(c->d.tab_sweep, sw.data(), sw.size() * sizeof(ApplyRow), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1020,6 +1053,16 @@ cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working
     cudaError_t e = tc_scale(c, S, r);
     if (e != cudaSuccess) return e;
   }
+  if (mode == kModeFP32 && !c->P.plr && c->sweep_fusable && c->opt_sweep == 0 && !g_shared_gpu) {
+    // all steps in one cooperative launch (the counter reset is the second operation)
+    cudaError_t e = cudaSuccess;
+    if (c->d.sweep_y32 &&
+        launch_sweep_f32(c->P.nt, c->P.ld32, c->P.T4, steps, c->d.tab_sweep, c->d.blocks_hi, r, y, c->d.sweep_y32, S,
+                         c->d.sweep_bar, c->d.status, c->stream, &e)) {
+      c->launches += 2;
+      return e;
+    }
+  }
   for (int s = 0; s < steps; ++s) {
     cudaError_t e = apply(c, mode, op_sweep(c, s), S, y, r, y, kApplyRowsSweep, 1.0, 0.0, working);
     if (e != cudaSuccess) return e;
@@ -1136,6 +1179,11 @@ extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
   if (option == PT_OPT_LOCAL_SOLVE) {
     if (value < 0 || value > 3) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0, 1, 2 or 3");
     ctx->opt_local_solve = value;
+    return PT_OK;
+  }
+  if (option == PT_OPT_SWEEP) {
+    if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_SWEEP must be 0 or 1");
+    ctx->opt_sweep = value;
     return PT_OK;
   }
   if (option == PT_OPT_LAYER_GROUP) {
@@ -1616,10 +1664,12 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     PT_CUDA(cudaMemcpyAsync(B.kk, kk.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
     c->launches += 2;
     PT_CUDA(launch_lsq_combine(S, m, B.kk, B.H, B.g, B.y, B.Z, N, B.x, s));
-    // explicit residual r = P b - P M x between restart cycles (iterative refinement): FP64 blocks,
-    // or in PT_MIXED_TC the double-float product (~1e-14) on the FP32 pipes, since the tensor-core
-    // matvec of the inner cycles is only ~1e-5 accurate
-    if (tcmode(c)) PT_CUDA(apply(c, kModeDF, op_matvec(c), S, B.x, nullptr, B.t, kApplyRowsWide, 1.0, 0.0, false));
+    // explicit residual r = P b - P M x between restart cycles (iterative refinement): FP64 blocks
+    // in PT_FP64 and with compressed blocks; in the mixed forms the double-float product (~1e-14)
+    // on the FP32 pipes (the FP64 pipe bounds an FP64 product at about twice its time), which in
+    // PT_MIXED_TC also corrects the ~1e-5 tensor-core matvec of the inner cycles
+    if (mixed(c) && !c->P.plr)
+      PT_CUDA(apply(c, kModeDF, op_matvec(c), S, B.x, nullptr, B.t, kApplyRowsWide, 1.0, 0.0, false));
     else PT_CUDA(do_matvec(c, S, B.x, B.t));
     c->launches += 2;
     PT_CUDA(launch_sub(B.b, B.t, B.w, S * N, s));
@@ -1692,6 +1742,7 @@ extern "C" pt_status pt_solve_many(int32_t nctx, pt_ctx* const* ctxs, const int3
   std::vector<pt_status> st(nctx, PT_OK);
   std::vector<std::string> msg(nctx);
   auto work = [&](int k) {
+    g_shared_gpu = true;
     if (cudaSetDevice(dev) != cudaSuccess) {
       st[k] = PT_ERR_CUDA;
       msg[k] = "cudaSetDevice failed";

@@ -20,6 +20,8 @@
 // sources fastest so that a batch of sources shares each block row through L2.
 #include "pt_common.cuh"
 
+#include <algorithm>
+
 namespace pt {
 
 enum ApplyMode { kFP64 = 0, kFP32 = 1, kDF = 2 };
@@ -339,6 +341,294 @@ bool launch_apply_f32_rows(int nt, int ld, int T4, const ApplyRow* table, int nr
     return false;
   }
   *err = cudaGetLastError();
+  return true;
+}
+
+// ---- FP32 D^{-1} in one launch: every sweep step of a cooperative grid ---------
+// The steps of a sweep (Section 4.1) form a chain: step s reads the traces that step
+// s-1 wrote.  One launch per step pays a launch gap and a full HBM round trip per step
+// although the block rows a step multiplies do not depend on the chain.  Here a grid
+// that is co-resident (cooperative launch) runs all L-1 steps; warp w of the grid owns
+// row rho = w of every step's 4 n_t rows (rho / n_t picks the output trace, rho % n_t
+// the row).  As soon as its CTA has finished a step, the warp asks the copy engine for
+// its two block rows of the next step (bulk asynchronous copies into shared memory,
+// completion on an mbarrier): the next step's HBM stream runs during the grid barrier
+// and the staging of the new inputs, and it does not hold the SM's load slots, which
+// register loads of 141 KB per SM would exhaust.  The grid barrier is one arrival
+// counter, zeroed before the launch; every wait is bounded (kErrTimeout, then the grid
+// returns, after its own copies have landed).
+// Layout the host checks before it takes this path: rows 2g and 2g+1 of a step (g = 0:
+// the down-going pair, g = 1: the up-going pair) have the same terms (input trace, sign)
+// and differ only in their blocks; a term has one input trace; identities read the
+// auxiliary vector; alpha = 1, beta = 0; every row has a warp (4 n_t <= 16 x grid).
+constexpr int kSweepThreads = 512;
+constexpr int kSweepWarps = kSweepThreads / 32;
+
+__device__ __forceinline__ unsigned long long sweep_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned sweep_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sweep_arrive(unsigned* p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ uint32_t sweep_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// wait for phase `parity` of the copy mbarrier, at most 1 s; false (and kErrTimeout) on expiry
+__device__ __forceinline__ bool sweep_mb_wait(uint64_t* mb, int parity, int* status) {
+  const unsigned long long t0 = sweep_timer();
+  for (long long it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sweep_saddr(mb)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && sweep_timer() - t0 > 1000000000ull) break;
+  }
+  atomicOr(status, kErrTimeout);
+  return false;
+}
+
+template <int MAXC>
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    sweep_f32_kernel(int nt, int ld, int T4, int nsteps, const ApplyRow* __restrict__ table,
+                     const cf* __restrict__ blocks, const cd* __restrict__ aux, cd* y, cf* y32, int S,
+                     unsigned* bar, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int abort_flag;
+  // [step table: 4 nsteps rows][block rows: warp x term x ld][inputs: S x (2 g + t) x ld]
+  // [row sums: warp x S][one mbarrier per warp]
+  ApplyRow* tab = reinterpret_cast<ApplyRow*>(smem_raw);
+  cf* buf = reinterpret_cast<cf*>(smem_raw + (size_t)4 * nsteps * sizeof(ApplyRow));
+  cf* xin = buf + (size_t)kSweepWarps * 2 * ld;
+  cf* sums = xin + (size_t)S * 4 * ld;
+  uint64_t* mbs = reinterpret_cast<uint64_t*>(sums + (((size_t)kSweepWarps * S + 1) & ~(size_t)1));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kSweepWarps + warp;
+  const int Rn = 4 * nt;
+  const bool own = gw < Rn;
+  const int qt = own ? gw / nt : 0, r = own ? gw % nt : 0, g = qt >> 1;
+  const size_t vs = (size_t)T4 * nt;
+  const int np = ld >> 1;
+  // the pairs of output traces this CTA's rows touch
+  const int r_lo = blockIdx.x * kSweepWarps, r_hi = min(r_lo + kSweepWarps, Rn) - 1;
+  const int g_lo = r_lo / (2 * nt), g_hi = r_hi / (2 * nt);
+  const int ng = g_hi - g_lo + 1;
+  // output thread: (row w of this CTA, source q), w S + q = threadIdx.x < kSweepWarps S.  The
+  // FP64 part of a row (the identity terms) runs here, on few warps: one warp-wide FP64
+  // instruction occupies the SM's FP64 pipe for 16 cycles on this part.
+  const bool outer = threadIdx.x < kSweepWarps * S;
+  const int ow = outer ? threadIdx.x / S : 0, oq = threadIdx.x - ow * S;
+  const int orow = r_lo + ow;
+  const bool oown = outer && orow < Rn;
+  const int oqt = oown ? orow / nt : 0, or_ = oown ? orow % nt : 0;
+  {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(table);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(tab);
+    const int nw = (int)(4 * nsteps * sizeof(ApplyRow) / 8);
+    for (int i = threadIdx.x; i < nw; i += kSweepThreads) dst[i] = src[i];
+  }
+  uint64_t* mb = mbs + warp;  // this warp's copies
+  if (threadIdx.x == 0) abort_flag = 0;
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sweep_saddr(mb)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // lane 0 of every warp: its block rows of step st by the copy engine, on its own mbarrier
+  // (one arrival per phase, with the bytes it asked for), so that each warp starts its
+  // products as soon as its rows have landed; output threads: their identity terms
+  double2 a[2];
+  auto issue = [&](int st) {
+    if (lane == 0) {
+      const ApplyRow* row = tab + 4 * st + qt;
+      const int nterms = own ? row->nterms : 0;
+      const uint32_t bytes = (uint32_t)(nterms * ld * sizeof(cf));
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of the buffer first
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sweep_saddr(mb)), "r"(bytes)
+                   : "memory");
+      for (int t = 0; t < nterms; ++t)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                sweep_saddr(buf + (size_t)(warp * 2 + t) * ld)),
+            "l"(blocks + ((size_t)row->t[t].block * nt + r) * ld), "r"((uint32_t)(ld * sizeof(cf))),
+            "r"(sweep_saddr(mb))
+            : "memory");
+    }
+    const ApplyRow* orw = tab + 4 * st + oqt;
+    const int nid = orw->nid;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      double2 v = make_double2(0.0, 0.0);
+      if (oown && e < nid) v = __ldg(aux + (size_t)oq * vs + (size_t)orw->id_trace[e] * nt + or_);
+      a[e] = v;
+    }
+  };
+
+  issue(0);
+  for (int s = 0; s < nsteps; ++s) {
+    const ApplyRow* rows = tab + 4 * s;
+    if (s > 0) {  // grid barrier: every output of step s-1 is written
+      if (threadIdx.x == 0) {
+        const unsigned target = (unsigned)s * gridDim.x;
+        const unsigned long long t0 = sweep_timer();
+        for (long long it = 0;; ++it) {
+          if (sweep_ld_acquire(bar) >= target) break;
+          if ((it & 255) == 255 && sweep_timer() - t0 > 1000000000ull) {
+            atomicOr(status, kErrTimeout);
+            abort_flag = 1;
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      if (abort_flag) {  // let this step's copies land before the shared memory goes away
+        sweep_mb_wait(mb, s & 1, status);
+        return;
+      }
+    }
+    // (1) stage sign_t y32[in_t] of the touched pairs (the complex64 copies of the traces that
+    //     the previous steps wrote, read from L2), zero-padded to ld: slot j = 2 (g - g_lo) + t
+    //     of source q; two (q, j) pairs at a time, a thread's loads before its stores
+    {
+      const int nslot = 2 * ng, sh = ng == 2 ? 2 : 1, npair = S * nslot;
+      for (int p0 = 0; p0 < npair; p0 += 2) {
+        cf v[2][2];
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          const int p = p0 + pp, jj = p & (nslot - 1), q = p >> sh, t = jj & 1;
+          const ApplyRow* pr = rows + 2 * (g_lo + (jj >> 1));
+          const bool live = p < npair && t < pr->nterms;
+          const cf* src = y32 + (size_t)q * vs + (size_t)(live ? pr->t[t].in1 : 0) * nt;
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int k = threadIdx.x + u * kSweepThreads;
+            v[pp][u] = (live && k < nt) ? __ldcg(src + k) : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          const int p = p0 + pp, jj = p & (nslot - 1), q = p >> sh, t = jj & 1;
+          if (p < npair) {
+            const ApplyRow* pr = rows + 2 * (g_lo + (jj >> 1));
+            const float sg = t < pr->nterms ? (float)pr->t[t].sign : 0.f;
+            cf* dst = xin + ((size_t)q * 4 + 2 * g_lo + jj) * ld;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int k = threadIdx.x + u * kSweepThreads;
+              if (k < ld) dst[k] = make_float2(sg * v[pp][u].x, sg * v[pp][u].y);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // (2) this warp's block rows landed, (3) its row products (FP32), one sum per source
+    //     into shared memory
+    const bool ok = sweep_mb_wait(mb, s & 1, status);
+    if (own && ok) {
+      const int nterms = rows[qt].nterms;
+      for (int q = 0; q < S; ++q) {
+        float are = 0.f, aim = 0.f;
+        const float4* xv4 = reinterpret_cast<const float4*>(xin + (size_t)q * 4 * ld);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (t < nterms) {
+            const float4* bv4 = reinterpret_cast<const float4*>(buf + (size_t)(warp * 2 + t) * ld);
+#pragma unroll
+            for (int c = 0; c < MAXC; ++c) {
+              const int k = lane + 32 * c;
+              if (k < np) {
+                const float4 v = xv4[(2 * g + t) * np + k], bv = bv4[k];
+                are = fmaf(bv.x, v.x, are);
+                are = fmaf(-bv.y, v.y, are);
+                are = fmaf(bv.z, v.z, are);
+                are = fmaf(-bv.w, v.w, are);
+                aim = fmaf(bv.x, v.y, aim);
+                aim = fmaf(bv.y, v.x, aim);
+                aim = fmaf(bv.z, v.w, aim);
+                aim = fmaf(bv.w, v.z, aim);
+              }
+            }
+          }
+        }
+        const cf acc = warp_sum_cf(make_float2(are, aim));
+        if (lane == 0) sums[warp * S + q] = acc;
+      }
+    }
+    if (__syncthreads_or(!ok)) return;
+    // (4) outputs: y = sum + identity terms (FP64), and its complex64 copy for the next steps
+    if (oown) {
+      const ApplyRow* row = rows + oqt;
+      const cf acc = sums[ow * S + oq];
+      cd val = make_double2(acc.x, acc.y);
+      const int nid = row->nid;
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        if (e < nid) val = cadd(val, cscale(a[e], row->id_sign[e]));
+      const size_t o = (size_t)oq * vs + (size_t)row->out * nt + or_;
+      y[o] = val;
+      y32[o] = make_float2((float)val.x, (float)val.y);
+    }
+    // (5) arrive (a release: it waits for this CTA's stores), then the next step's copies,
+    //     which must not be in flight while the release drains the SM's memory operations
+    __syncthreads();
+    if (s + 1 < nsteps) {
+      if (threadIdx.x == 0) sweep_arrive(bar);
+      __syncthreads();
+      issue(s + 1);
+    }
+  }
+}
+
+size_t sweep_f32_smem(int ld, int S, int nsteps) {
+  return (size_t)4 * nsteps * sizeof(ApplyRow) + (size_t)kSweepWarps * 2 * ld * sizeof(cf) +
+         (size_t)S * 4 * ld * sizeof(cf) + ((((size_t)kSweepWarps * S + 1) & ~(size_t)1) * sizeof(cf)) +
+         kSweepWarps * sizeof(uint64_t);
+}
+
+// D^{-1} of the FP32 preconditioner in one cooperative launch; y32 (S x T4 x n_t complex64)
+// is scratch.  False (nothing launched) when the shape is outside the kernel's bounds
+// (register tile, shared memory, one warp per row of a step on a co-resident grid).
+bool launch_sweep_f32(int nt, int ld, int T4, int nsteps, const ApplyRow* table, const void* blocks, const cd* aux,
+                      cd* y, cf* y32, int S, unsigned* bar, int* status, cudaStream_t s, cudaError_t* err) {
+  const int np = ld >> 1;
+  if (nsteps < 1 || nsteps > 64 || S < 1 || S > 32 || ld > 2 * kSweepThreads) return false;
+  const void* fn;
+  if (np <= 32 * 4) fn = reinterpret_cast<const void*>(sweep_f32_kernel<4>);
+  else if (np <= 32 * 9) fn = reinterpret_cast<const void*>(sweep_f32_kernel<9>);
+  else return false;
+  const size_t smem = sweep_f32_smem(ld, S, nsteps);
+  int dev = 0, sms = 0, occ = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess && smem + 64 > (size_t)optin) return false;
+  if (e == cudaSuccess) e = smem_limit_max(fn);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSweepThreads, smem);
+  if (e != cudaSuccess) {
+    *err = e;
+    return true;
+  }
+  const int R = 4 * nt;
+  const int G = (R + kSweepWarps - 1) / kSweepWarps;
+  if (occ < 1 || G > sms * occ) return false;
+  e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    const ApplyRow* tb = table;
+    const cf* bl = static_cast<const cf*>(blocks);
+    void* args[] = {(void*)&nt, (void*)&ld, (void*)&T4, (void*)&nsteps, (void*)&tb, (void*)&bl,
+                    (void*)&aux, (void*)&y, (void*)&y32, (void*)&S, (void*)&bar, (void*)&status};
+    e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kSweepThreads), args, smem, s);
+  }
+  *err = e;
   return true;
 }
 

@@ -136,6 +136,36 @@ def test_mixed_local_solve_variants_match_oracle(small, variant, tol_field):
         assert _rel(u.cpu().numpy()[s], S.global_solve(prob, f[s])) < tol_field
 
 
+@pytest.mark.parametrize("nsrc", [1, 3])
+def test_one_launch_sweeps_match_per_step_sweeps_and_oracle(small, nsrc):
+    """The FP32 preconditioner with all sweep steps in one cooperative launch (default) against one launch
+    per step (the same products in the same order) and against Algorithm 4 of the oracle."""
+    from paper_1410_5910_gb300 import PT_OPT_SWEEP
+
+    wl, prob, _, off = small
+    _, solver = _mk(wl, precision=1, max_sources=nsrc)
+    x = _rand_vec(solver, 5, nsrc)
+    xt = torch.from_numpy(x).cuda()
+    fused = solver.precond(xt).cpu().numpy()
+    solver.set_option(PT_OPT_SWEEP, 1)
+    stepped = solver.precond(xt).cpu().numpy()
+    sp_ = off.split
+    for q in range(nsrc):
+        assert _rel(fused[q], stepped[q]) < 1e-12
+        unperm = np.empty_like(x[q])
+        unperm[sp_.perm] = x[q]
+        ref = polarized.gauss_seidel_preconditioner(sp_, unperm.ravel(), 2)
+        assert _rel(fused[q].ravel(), ref) < 1e-5
+    # and a whole solve with each
+    f = wl.f()
+    solver.set_option(PT_OPT_SWEEP, 0)
+    u0, _, its0, rel0 = solver.solve(torch.from_numpy(f).cuda(), tol=1e-10)
+    solver.set_option(PT_OPT_SWEEP, 1)
+    u1, _, its1, rel1 = solver.solve(torch.from_numpy(f).cuda(), tol=1e-10)
+    assert its0[0] == its1[0] and rel0[0] <= 1e-10
+    assert _rel(u0.cpu().numpy(), u1.cpu().numpy()) < 1e-9
+
+
 def test_batched_sources_equal_single_solves():
     wl = W.small_case(40, 60, 8, 3, medium="grf", seed=11)
     prob, solver = _mk(wl, max_sources=3)
