@@ -83,6 +83,9 @@ cudaError_t nn_sumsq(const float*, long, double*, cudaStream_t);
 cudaError_t nn_scale(float*, long, float, cudaStream_t);
 bool launch_apply_f32_rows(int, int, int, const ApplyRow*, int, const void*, const cd*, const cd*, cd*, int, double,
                            double, cudaStream_t, cudaError_t*);
+cudaError_t launch_prep_inputs(const cd*, int, int, int, bool, void*, cudaStream_t);
+cudaError_t launch_apply_lowp(int, int, int, int, const ApplyRow*, int, const cf*, const cf*, const void*, const cd*,
+                              const cd*, cd*, int, int, double, double, cudaStream_t);
 bool launch_sweep_f32(int, int, int, int, const ApplyRow*, const void*, const cd*, cd*, cf*, int, unsigned*, int*,
                       cudaStream_t, cudaError_t*);
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
@@ -256,6 +259,7 @@ struct Persist {
   int* status;
   unsigned* sweep_bar;  // grid-barrier counter of the one-launch sweeps
   cf* sweep_y32;        // complex64 copies of the traces a one-launch sweep writes (mixed FP32 form)
+  void* xprep;          // inputs of the FP32 / double-float applies converted once per application
   cd* W;
   cd* E;
   cd* Sinv;
@@ -326,6 +330,7 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
     q.e_lo = c.take<cf>(P.coef_elems);
   }
   if (p->precision == PT_MIXED_FP32 && !P.plr) q.sweep_y32 = c.take<cf>((size_t)p->max_sources * P.T4 * P.nt);
+  if (p->precision != PT_FP64 && !P.plr) q.xprep = c.take<float4>((size_t)p->max_sources * P.T4 * P.ld32);
   q.tab_matvec = c.take<ApplyRow>(P.T4);
   q.tab_R = c.take<ApplyRow>(P.T4);
   q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
@@ -987,6 +992,14 @@ cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, cons
     if (launch_apply_f32_rows(P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, x, aux, y, S, alpha, beta,
                               c->stream, &e))
       return e;
+  }
+  if ((mode == kModeFP32 || mode == kModeDF) && c->d.xprep && !P.plr) {
+    // inputs converted once, FP32 staging, FP64 epilogue on one thread per row
+    c->launches++;
+    cudaError_t e = launch_prep_inputs(x, S * P.T4, P.nt, P.ld32, mode == kModeDF, c->d.xprep, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_apply_lowp(mode, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, c->d.blocks_lo,
+                             c->d.xprep, x, aux, y, S, rows_per_cta, alpha, beta, c->stream);
   }
   return launch_apply_mode(mode, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, c->d.blocks_lo, x, aux, y,
                            S, rows_per_cta, alpha, beta, c->stream);

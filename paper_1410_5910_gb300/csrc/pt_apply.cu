@@ -232,6 +232,243 @@ __global__ void __launch_bounds__(256) apply_kernel(int nt, int ld, int T4, cons
   }
 }
 
+// ---- FP32 and double-float applies on inputs converted once ---------------------------
+// GB300 issues FP64 instructions at 2 lanes per clock per SM: a warp-wide FP64 instruction
+// holds the SM's FP64 pipe for 16 cycles.  Converting every staged input element from
+// FP64 in each CTA (35 row tiles per output trace read the same inputs) and running the
+// FP64 epilogue of every row on its warp made these HBM-bound applies wait on that pipe.
+// Here one pass converts x once per application into xp (DF: float4 (re_hi, im_hi,
+// re_lo, im_lo), hi = fl32(v), lo = fl32(v - hi); FP32: float2), rows padded to ld with
+// zeros; the apply CTAs stage sign (xp[in1] + xp[in2]) with FP32 (DF: error-free two-sum)
+// arithmetic, keep the warp sums in shared memory and let one thread per row add the
+// identity terms and the alpha / beta combination in FP64.
+__global__ void prep_inputs_kernel(const cd* __restrict__ x, int nt, int ld, int df, void* __restrict__ xp) {
+  const size_t v = blockIdx.y;  // source x trace
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ld; k += gridDim.x * blockDim.x) {
+    const cd a = k < nt ? x[v * nt + k] : make_double2(0.0, 0.0);
+    const float rh = (float)a.x, ih = (float)a.y;
+    if (df)
+      reinterpret_cast<float4*>(xp)[v * ld + k] =
+          make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
+    else
+      reinterpret_cast<float2*>(xp)[v * ld + k] = make_float2(rh, ih);
+  }
+}
+
+cudaError_t launch_prep_inputs(const cd* x, int nvec, int nt, int ld, bool df, void* xp, cudaStream_t s) {
+  dim3 grid((ld + 255) / 256, nvec);
+  prep_inputs_kernel<<<grid, 256, 0, s>>>(x, nt, ld, df ? 1 : 0, xp);
+  return cudaGetLastError();
+}
+
+// (hi, lo) = a + b for double-float numbers (two-sum of the high parts, low parts folded
+// in, renormalised); about 2^-46 relative
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) apply_lowp_kernel(int nt, int ld, int T4, const ApplyRow* __restrict__ table,
+                                                         const cf* __restrict__ blocks_a,
+                                                         const cf* __restrict__ blocks_b,
+                                                         const void* __restrict__ xp, const cd* x,
+                                                         const cd* __restrict__ aux, cd* y, int rows_per_cta,
+                                                         double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ApplyRow row;
+  if (threadIdx.x == 0) row = table[blockIdx.z];
+  __syncthreads();
+  const int s = blockIdx.x;
+  const size_t vs = (size_t)T4 * nt;
+  const size_t bsz = (size_t)nt * ld;
+  const int nterms = row.nterms;
+  const int np = ld >> 1;
+  // per-row warp sums after the staged inputs: DF (S_re, C_re, S_im, C_im), FP32 (re, im)
+  float4* res = reinterpret_cast<float4*>(smem_raw + (size_t)nterms * ld * (MODE == kDF ? 16 : 8));
+
+  // ---- stage sign_t (xp[in1] + xp[in2]) for every term, FP32 arithmetic only
+  for (int t = 0; t < nterms; ++t) {
+    const ApplyTerm tm = row.t[t];
+    const float sg = (float)tm.sign;  // +-1: exact
+    if (MODE == kDF) {
+      const float4* a = reinterpret_cast<const float4*>(xp) + ((size_t)s * T4 + tm.in1) * ld;
+      const float4* b = tm.in2 >= 0 ? reinterpret_cast<const float4*>(xp) + ((size_t)s * T4 + tm.in2) * ld : nullptr;
+      for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+        float4 v = a[k];
+        if (b) {
+          const float4 w = b[k];
+          float rh, rl, ih, il;
+          df_add(v.x, v.z, w.x, w.z, rh, rl);
+          df_add(v.y, v.w, w.y, w.w, ih, il);
+          v = make_float4(rh, ih, rl, il);
+        }
+        reinterpret_cast<float4*>(smem_raw)[t * ld + k] = make_float4(sg * v.x, sg * v.y, sg * v.z, sg * v.w);
+      }
+    } else {
+      const float2* a = reinterpret_cast<const float2*>(xp) + ((size_t)s * T4 + tm.in1) * ld;
+      const float2* b = tm.in2 >= 0 ? reinterpret_cast<const float2*>(xp) + ((size_t)s * T4 + tm.in2) * ld : nullptr;
+      for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+        float2 v = a[k];
+        if (b) {
+          const float2 w = b[k];
+          v = make_float2(v.x + w.x, v.y + w.y);
+        }
+        reinterpret_cast<float2*>(smem_raw)[t * ld + k] = make_float2(sg * v.x, sg * v.y);
+      }
+    }
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * rows_per_cta;
+  for (int rr = warp; rr < rows_per_cta; rr += 8) {
+    const int r = r0 + rr;
+    if (r >= nt) break;
+    if (MODE == kFP32) {
+      const float4* xin = reinterpret_cast<const float4*>(smem_raw);  // two complex64 per float4
+      float are = 0.f, aim = 0.f;
+      for (int t = 0; t < nterms; ++t) {
+        const float4* B = reinterpret_cast<const float4*>(blocks_a + (size_t)row.t[t].block * bsz + (size_t)r * ld);
+        const float4* xv = xin + t * np;
+        int k = lane;
+        for (; k + 96 < np; k += 128) {
+          float4 b[4], v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) b[u] = __ldg(B + k + 32 * u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            v[u] = xv[k + 32 * u];
+            are = fmaf(b[u].x, v[u].x, are);
+            are = fmaf(-b[u].y, v[u].y, are);
+            are = fmaf(b[u].z, v[u].z, are);
+            are = fmaf(-b[u].w, v[u].w, are);
+            aim = fmaf(b[u].x, v[u].y, aim);
+            aim = fmaf(b[u].y, v[u].x, aim);
+            aim = fmaf(b[u].z, v[u].w, aim);
+            aim = fmaf(b[u].w, v[u].z, aim);
+          }
+        }
+        for (; k < np; k += 32) {
+          float4 b = __ldg(B + k), v = xv[k];
+          are = fmaf(b.x, v.x, are);
+          are = fmaf(-b.y, v.y, are);
+          are = fmaf(b.z, v.z, are);
+          are = fmaf(-b.w, v.w, are);
+          aim = fmaf(b.x, v.y, aim);
+          aim = fmaf(b.y, v.x, aim);
+          aim = fmaf(b.z, v.w, aim);
+          aim = fmaf(b.w, v.z, aim);
+        }
+      }
+      const cf acc = warp_sum_cf(make_float2(are, aim));
+      if (lane == 0) res[rr] = make_float4(acc.x, acc.y, 0.f, 0.f);
+    } else {
+      const float4* xin = reinterpret_cast<const float4*>(smem_raw);  // (re_hi, im_hi, re_lo, im_lo)
+      float Sr = 0.f, Cr = 0.f, Si = 0.f, Ci = 0.f;
+      float Sr2 = 0.f, Cr2 = 0.f, Si2 = 0.f, Ci2 = 0.f;
+      for (int t = 0; t < nterms; ++t) {
+        const size_t off = (size_t)row.t[t].block * bsz + (size_t)r * ld;
+        const float4* H = reinterpret_cast<const float4*>(blocks_a + off);
+        const float4* Lo = reinterpret_cast<const float4*>(blocks_b + off);
+        const float4* xv = xin + t * ld;
+        int k = lane;
+        for (; k + 32 < np; k += 64) {
+          const float4 h0 = __ldg(H + k), l0 = __ldg(Lo + k), h1 = __ldg(H + k + 32), l1 = __ldg(Lo + k + 32);
+          const float4 a0 = xv[2 * k], a1 = xv[2 * k + 1];
+          const float4 b0 = xv[2 * (k + 32)], b1 = xv[2 * (k + 32) + 1];
+          df_mac(h0.x, l0.x, a0.x, a0.z, Sr, Cr);
+          df_mac(h1.x, l1.x, b0.x, b0.z, Sr2, Cr2);
+          df_mac(h0.x, l0.x, a0.y, a0.w, Si, Ci);
+          df_mac(h1.x, l1.x, b0.y, b0.w, Si2, Ci2);
+          df_mac(-h0.y, -l0.y, a0.y, a0.w, Sr, Cr);
+          df_mac(-h1.y, -l1.y, b0.y, b0.w, Sr2, Cr2);
+          df_mac(h0.y, l0.y, a0.x, a0.z, Si, Ci);
+          df_mac(h1.y, l1.y, b0.x, b0.z, Si2, Ci2);
+          df_mac(h0.z, l0.z, a1.x, a1.z, Sr, Cr);
+          df_mac(h1.z, l1.z, b1.x, b1.z, Sr2, Cr2);
+          df_mac(h0.z, l0.z, a1.y, a1.w, Si, Ci);
+          df_mac(h1.z, l1.z, b1.y, b1.w, Si2, Ci2);
+          df_mac(-h0.w, -l0.w, a1.y, a1.w, Sr, Cr);
+          df_mac(-h1.w, -l1.w, b1.y, b1.w, Sr2, Cr2);
+          df_mac(h0.w, l0.w, a1.x, a1.z, Si, Ci);
+          df_mac(h1.w, l1.w, b1.x, b1.z, Si2, Ci2);
+        }
+        for (; k < np; k += 32) {
+          const float4 h = __ldg(H + k), l = __ldg(Lo + k);
+          const float4 x0 = xv[2 * k], x1 = xv[2 * k + 1];
+          df_mac(h.x, l.x, x0.x, x0.z, Sr, Cr);
+          df_mac(-h.y, -l.y, x0.y, x0.w, Sr, Cr);
+          df_mac(h.x, l.x, x0.y, x0.w, Si, Ci);
+          df_mac(h.y, l.y, x0.x, x0.z, Si, Ci);
+          df_mac(h.z, l.z, x1.x, x1.z, Sr, Cr);
+          df_mac(-h.w, -l.w, x1.y, x1.w, Sr, Cr);
+          df_mac(h.z, l.z, x1.y, x1.w, Si, Ci);
+          df_mac(h.w, l.w, x1.x, x1.z, Si, Ci);
+        }
+      }
+      {  // merge the second set: (S, C) += (S2, C2)
+        float s1, e1;
+        two_sum(Sr, Sr2, s1, e1);
+        Sr = s1;
+        Cr = Cr + Cr2 + e1;
+        two_sum(Si, Si2, s1, e1);
+        Si = s1;
+        Ci = Ci + Ci2 + e1;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        df_shfl_add(Sr, Cr, o);
+        df_shfl_add(Si, Ci, o);
+      }
+      if (lane == 0) res[rr] = make_float4(Sr, Cr, Si, Ci);
+    }
+  }
+  __syncthreads();
+  // ---- FP64 epilogue, one thread per row
+  const int rr = threadIdx.x;
+  const int r = r0 + rr;
+  if (rr < rows_per_cta && r < nt) {
+    const float4 v = res[rr];
+    cd val = MODE == kDF ? make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w)
+                         : make_double2(v.x, v.y);
+    const cd* xs = x + s * vs;
+    const cd* as = aux ? aux + s * vs : nullptr;
+    for (int e = 0; e < row.nid; ++e) {
+      const cd* src = row.id_src[e] == 0 ? xs : as;
+      val = cadd(val, cscale(src[(size_t)row.id_trace[e] * nt + r], row.id_sign[e]));
+    }
+    val = cscale(val, alpha);
+    if (beta != 0.0) val = cadd(val, cscale(as[(size_t)row.out * nt + r], beta));
+    y[s * vs + (size_t)row.out * nt + r] = val;
+  }
+}
+
+cudaError_t launch_apply_lowp(int mode, int nt, int ld, int T4, const ApplyRow* table, int nrows, const cf* blocks_a,
+                              const cf* blocks_b, const void* xp, const cd* x, const cd* aux, cd* y, int nsrc,
+                              int rows_per_cta, double alpha, double beta, cudaStream_t s) {
+  if (rows_per_cta > 256) return cudaErrorInvalidValue;
+  const int elem = mode == kDF ? 16 : 8;
+  const size_t smem = 4ull * ld * elem + (size_t)rows_per_cta * sizeof(float4);
+  dim3 grid(nsrc, (nt + rows_per_cta - 1) / rows_per_cta, nrows);
+  cudaError_t e;
+  if (mode == kDF) {
+    e = smem_limit_max(reinterpret_cast<const void*>(apply_lowp_kernel<kDF>));
+    if (e != cudaSuccess) return e;
+    apply_lowp_kernel<kDF><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, xp, x, aux, y,
+                                                   rows_per_cta, alpha, beta);
+  } else {
+    e = smem_limit_max(reinterpret_cast<const void*>(apply_lowp_kernel<kFP32>));
+    if (e != cudaSuccess) return e;
+    apply_lowp_kernel<kFP32><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, xp, x, aux, y,
+                                                     rows_per_cta, alpha, beta);
+  }
+  return cudaGetLastError();
+}
+
 // ---- FP32 sweep steps: one row per warp, whole block rows in flight ---------------
 // A sweep step (Section 4.1) is small (8 blocks): the time is memory latency, not
 // bandwidth.  Each lane issues the loads of its share of both terms' block rows into

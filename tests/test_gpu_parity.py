@@ -166,6 +166,23 @@ def test_one_launch_sweeps_match_per_step_sweeps_and_oracle(small, nsrc):
     assert _rel(u0.cpu().numpy(), u1.cpu().numpy()) < 1e-9
 
 
+@pytest.mark.parametrize("nsrc", [1, 3])
+def test_mixed_working_operators_match_oracle(small, nsrc):
+    """The operators PT_MIXED_FP32 iterates with: double-float P M (~1e-14), FP32 R and D^{-1} (~1e-7), against
+    the oracle's FP64 operators."""
+    wl, prob, _, off = small
+    _, solver = _mk(wl, precision=1, max_sources=nsrc)
+    x = _rand_vec(solver, 21, nsrc)
+    xt = torch.from_numpy(x).cuda()
+    sp_ = off.split
+    got = {w: solver.apply(w, xt, working=True).cpu().numpy() for w in ("matvec", "R", "Dinv")}
+    for q in range(nsrc):
+        xs = x[q].ravel()
+        assert _rel(got["matvec"][q].ravel(), sp_.PM.apply(xs)) < 1e-12
+        assert _rel(got["R"][q].ravel(), sp_.apply_R(xs)) < 2e-6
+        assert _rel(got["Dinv"][q].ravel(), sp_.solve_D(xs)) < 2e-6
+
+
 def test_batched_sources_equal_single_solves():
     wl = W.small_case(40, 60, 8, 3, medium="grf", seed=11)
     prob, solver = _mk(wl, max_sources=3)
