@@ -464,9 +464,33 @@ def main():
     nt = wl.nt
     nb = [int(v) for v in np.diff(np.asarray(layer_partition(wl.nx, wl.nz, wl.npml, L_)))]
     nloc = [n_ + (wl.npml if l_ > 0 else 0) + (wl.npml if l_ < L_ - 1 else 0) for l_, n_ in enumerate(nb)]
+    roof_ls = None
     if chosen_prec == PT_MIXED_FP32:
-        # local solves (reconstruction launch: every layer, 2 n_t - 1 dependent steps), timed live as the
-        # difference of solves with and without the volume output
+        # (1) the double-float matvec P M x of the GMRES iterations and restart residuals (the largest share
+        #     of a solve): one pt_apply call = the input conversion + apply_lowp_kernel<2>, timed live
+        nblocks = 16 * (L_ - 2) + 8
+        xm = torch.randn((S, solver.T4, solver.nt), dtype=torch.complex128, device=dev)
+        for _ in range(3):
+            solver.apply("matvec", xm, working=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        for a_, b_ in ev:
+            a_.record(stream)
+            solver.apply("matvec", xm, working=True)
+            b_.record(stream)
+        torch.cuda.synchronize(dev)
+        t_df = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
+        # algorithmic bytes: hi and lo complex64 copies of every block entry, the FP64 input and output
+        alg_df = nblocks * nt * nt * 16 + 2 * S * solver.T4 * nt * 16
+        roof = {"kernel": "apply_lowp_kernel<2> (double-float P M x, with its input conversion)", "bound": "hbm",
+                "achieved": alg_df / t_df / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": None,
+                # DRAM traffic of the same kernel on the 255 x 511, L = 8 layered case (ncu): 1.00 x its
+                # algorithmic bytes; it grows with the block bytes, so it is scaled
+                "traffic": 1.00 * alg_df, "algorithmic_bytes": alg_df, "launch_ms": t_df * 1e3,
+                "traffic_source": "scaled from the ncu capture of the layered-255x511-L8 case"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        # (2) the chunked local solves of the reconstruction (every layer, K_v chunks of n_t / K_v columns,
+        #     two passes and the boundary propagation), timed live as the difference of solves with and
+        #     without the volume output
         u_tmp = torch.empty_like(f_dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
         t_with, t_without = [], []
@@ -481,26 +505,27 @@ def main():
             t_with.append(ev[0][0].elapsed_time(ev[0][1]))
             t_without.append(ev[1][0].elapsed_time(ev[1][1]))
         t_launch = (statistics.median(t_with) - statistics.median(t_without)) / 1e3
-        # algorithmic bytes per launch: Sinv (complex64) of every column of every layer, read by the forward
-        # and again by the backward substitution (2 n_t - 1 column steps), the x-couplings, the forward
-        # iterates written and read back (complex64), the volume output and the trace forcing
-        steps = 2 * nt - 1
-        sinv = sum(steps * n_ * n_ * 8 for n_ in nloc)
-        coef = sum(2 * nt * n_ * 8 for n_ in nloc)
-        ystore = sum(2 * nt * n_ * 8 for n_ in nloc)
+        # chunks per layer as the library chooses them: at least 16 columns, about one CTA per SM
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        kv = max(1, min(max(1, min(64, nt // 16)), sms // L_))
+        # algorithmic bytes: Sinv (complex64) of every column read by the forward and the backward
+        # substitution of both passes, the transfer matrices of the propagation, couplings, stored
+        # iterates, the volume output and the trace forcing
+        sinv = sum(4 * nt * n_ * n_ * 8 for n_ in nloc)
+        trans = sum(3 * (kv - 1) * n_ * n_ * 8 for n_ in nloc)
+        coef = sum(2 * 2 * nt * n_ * 8 for n_ in nloc)
+        ystore = sum(2 * 2 * nt * n_ * 8 for n_ in nloc)
         vol = wl.Nz * nt * 16 + 4 * (L_ - 1) * nt * 16
-        alg = (sinv + coef + ystore + vol) * S
-        # DRAM traffic of the same kernel on the 255 x 511, L = 8 layered case (ncu): 0.80 x its
-        # algorithmic bytes (L2 serves the columns around the forward / backward turn); traffic grows
-        # with the units (column steps x rows^2), so it is scaled
-        traffic = 0.80 * alg
-        roof = {"kernel": "layer_solve_f32c_kernel<1, 4> (FP32 local solves on 4-CTA clusters, reconstruction)",
-                "bound": "hbm", "achieved": alg / t_launch / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": traffic, "algorithmic_bytes": alg, "launch_ms": t_launch * 1e3,
-                "latency_bound": f"{steps} dependent column steps, {t_launch / steps * 1e6:.2f} us per step",
-                "achieved_gflops": 8.0 * sum(n_ * n_ for n_ in nloc) * steps * S / t_launch / 1e9,
-                "traffic_source": "scaled from the ncu capture of the layered-255x511-L8 case"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
+        alg = (sinv + trans + coef + ystore + vol) * S
+        steps = 2 * 2 * -(-nt // kv)
+        roof_ls = {"kernel": "layer_solve_chunk_kernel<1, 1|3> + chunk_propagate_kernel (FP32 local solves chunked "
+                             "along x, reconstruction)", "bound": "hbm", "achieved": alg / t_launch / 1e9,
+                   "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": None, "traffic": None, "algorithmic_bytes": alg,
+                   "launch_ms": t_launch * 1e3, "chunks_per_layer": kv,
+                   "latency_bound": f"{steps} dependent column steps in two passes ({kv} chunks per layer) "
+                                    f"plus {2 * (kv - 1)} propagation products",
+                   "achieved_gflops": 8.0 * sum(n_ * n_ for n_ in nloc) * 2 * 2 * nt * S / t_launch / 1e9}
+        roof_ls["frac"] = roof_ls["achieved"] / roof_ls["peak"]
     else:
         roof = None
     # the interface-system matvec with FP64 blocks (the plain form's GEMV), one launch
@@ -570,7 +595,7 @@ def main():
                        "l2": f"interface blocks {16 * L_ * nt * nt * 16 / 1e9:.2f} GB stream from HBM each "
                              "iteration (> 129 MB L2); no flush needed"},
             "gmres_iterations": its, "true_relres": rel, "offline_s": t_off,
-            "roofline": roof, "roofline_fp64_matvec": roof64, "peaks_source": pk_kind, "clocks": clocks,
+            "roofline": roof, "roofline_local_solve": roof_ls, "roofline_fp64_matvec": roof64, "peaks_source": pk_kind, "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": int(launches * args.steps), "cpu_baseline": cpu,
         }

@@ -66,8 +66,9 @@ typedef enum {
   PT_MIXED_FP32 = 1, /* preconditioner (Algorithm 4) applies FP32 copies of the
                         blocks; the GMRES matvec runs in double-float (FP32 pairs,
                         ~1e-14); local solves (right-hand side, reconstruction) in
-                        FP32 with the FP64 factors rounded to complex64 (~1e-6 on
-                        the field; PT_OPT_LOCAL_SOLVE = 1 selects double-float);
+                        FP32 with the FP64 factors rounded to complex64, chunked
+                        along x (~1e-6 on the field; PT_OPT_LOCAL_SOLVE = 1
+                        selects double-float);
                         the explicit residual between restart cycles in double-float;
                         Arnoldi and least squares in FP64 (flexible GMRES).  With
                         compressed blocks (plr) the products are FP64 instead of
@@ -238,11 +239,15 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * PT_OPT_LEARNED: 1 = flexible GMRES adds the learned correction to the
  * preconditioner (needs learned = 1 at pt_create and weights, see below),
  * 0 = plain Algorithm 4 (default).
- * PT_OPT_LOCAL_SOLVE: local solves of PT_MIXED_FP32 - 0 = FP32 on a cluster
- * of 4 CTAs per (layer, source), each CTA holding a quarter of the rows of
- * the next column's factors in shared memory (default, ~1e-6 on the field);
- * 3 = the same on 8 CTAs; 2 = FP32 on one CTA; 1 = double-float on clusters
- * of 4 CTAs (~1e-13, slower).
+ * PT_OPT_LOCAL_SOLVE: local solves of PT_MIXED_FP32 - 4 = FP32, each layer's
+ * columns cut into chunks solved in parallel, one CTA per (layer, chunk,
+ * source): every chunk from zero boundary values, then the boundary values
+ * from chunk-transfer matrices formed at pt_create (FP64, kept in complex64),
+ * then every chunk again from its boundary values (default, ~1e-6 on the
+ * field); 0 = FP32 on a cluster of 4 CTAs per (layer, source), each CTA
+ * holding a quarter of the rows of the next column's factors in shared
+ * memory; 3 = the same on 8 CTAs; 2 = FP32 on one CTA; 1 = double-float on
+ * clusters of 4 CTAs (~1e-13, slower).
  * PT_OPT_SWEEP: the sweeps D^{-1} of the PT_MIXED_FP32 preconditioner -
  * 0 = all L-1 steps of a sweep in one cooperative launch with a grid barrier
  * between steps (default; used when the shape fits its register and shared-

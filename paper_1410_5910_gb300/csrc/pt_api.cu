@@ -83,6 +83,12 @@ cudaError_t nn_sumsq(const float*, long, double*, cudaStream_t);
 cudaError_t nn_scale(float*, long, float, cudaStream_t);
 bool launch_apply_f32_rows(int, int, int, const ApplyRow*, int, const void*, const cd*, const cd*, cd*, int, double,
                            double, cudaStream_t, cudaError_t*);
+size_t chunk_work_bytes(int, int, int);
+cudaError_t launch_chunk_transfer(const Geometry&, const LayerInfo*, const cd*, const cd*, const cd*, int, int, cd*,
+                                  cf*, cudaStream_t);
+cudaError_t launch_layer_solve_chunked(int, const Geometry&, const LayerInfo*, int, int, const cf*, const cf*,
+                                       const cf*, const cf*, const cd*, const cd*, cd*, size_t, cd*, const int*, cf*,
+                                       int, int*, cudaStream_t);
 cudaError_t launch_prep_inputs(const cd*, int, int, int, bool, void*, cudaStream_t);
 cudaError_t launch_apply_lowp(int, int, int, int, const ApplyRow*, int, const cf*, const cf*, const void*, const cd*,
                               const cd*, cd*, int, int, double, double, cudaStream_t);
@@ -91,7 +97,7 @@ bool launch_sweep_f32(int, int, int, int, const ApplyRow*, const void*, const cd
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
-cudaError_t launch_norm_scale(const cd*, size_t, int, double*, cd*, int, int, int, int, cd*, size_t,
+cudaError_t launch_norm_scale(const cd*, size_t, int, double*, cd*, int, int, int, int, cd*, size_t, double*,
                               cudaStream_t);
 cudaError_t launch_givens(int, int, int, cd*, double*, cd*, cd*, double*, cudaStream_t);
 cudaError_t launch_lsq_combine(int, int, const int*, const cd*, const cd*, cd*, const cd*, size_t, cd*,
@@ -162,6 +168,10 @@ struct Plan {
   // learned correction: inference buffers for nn_cs sources at a time
   bool learned = false;
   int nn_cs = 0;
+  // chunked local solves of the mixed FP32 form: chunks per layer of the right-hand side
+  // (one active layer per point source: short chains) and of the reconstruction (every
+  // layer at once: about one chunk per SM)
+  int kr = 0, kv = 0;
 };
 
 pt_status make_plan(const pt_params* p, Plan& P) {
@@ -220,6 +230,17 @@ pt_status make_plan(const pt_params* p, Plan& P) {
   }
   if (P.nloc_max > kMaxNloc)
     return fail(PT_ERR_ARG, "a local problem has more than 118 rows (layer rows + 2 n_pml); use more layers");
+  if (p->precision == PT_MIXED_FP32) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    const int kmax = std::max(1, std::min(64, P.nt / 16));  // chunks of at least 16 columns
+    P.kr = std::min(kmax, 32);
+    P.kv = std::max(1, std::min(kmax, sms / P.L));
+  }
   if (p->plr) {
     if (p->plr_rmax < 1 || p->plr_rmax > 31 || !(p->plr_eps > 0) || !std::isfinite(p->plr_eps))
       return fail(PT_ERR_ARG, "plr needs 1 <= plr_rmax <= 31 and plr_eps > 0");
@@ -260,6 +281,7 @@ struct Persist {
   unsigned* sweep_bar;  // grid-barrier counter of the one-launch sweeps
   cf* sweep_y32;        // complex64 copies of the traces a one-launch sweep writes (mixed FP32 form)
   void* xprep;          // inputs of the FP32 / double-float applies converted once per application
+  cf* chunk_T;          // Phi_k, M_k, Psi_k of the chunked local solves: [kr set | kv set][L][K][3][nloc_max^2]
   cd* W;
   cd* E;
   cd* Sinv;
@@ -331,6 +353,8 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
   }
   if (p->precision == PT_MIXED_FP32 && !P.plr) q.sweep_y32 = c.take<cf>((size_t)p->max_sources * P.T4 * P.nt);
   if (p->precision != PT_FP64 && !P.plr) q.xprep = c.take<float4>((size_t)p->max_sources * P.T4 * P.ld32);
+  if (P.kr > 0)
+    q.chunk_T = c.take<cf>((size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max + 64);  // + read slack
   q.tab_matvec = c.take<ApplyRow>(P.T4);
   q.tab_R = c.take<ApplyRow>(P.T4);
   q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
@@ -381,7 +405,8 @@ size_t setup_bytes_of(const Plan& P) {
   Carver c(nullptr);
   int nslots = std::min<int>((int)P.tasks.size(), kExtractSlots);
   c.take<cd>(setup_slot_elems(P) * nslots);
-  return c.off;
+  // the chunk transfer matrices are formed after the extraction, in the same scratch
+  return std::max(c.off, chunk_work_bytes(P.L, std::max(P.kr, P.kv), P.nloc_max));
 }
 
 // The PLR compressor reuses the setup workspace after the extraction.
@@ -397,6 +422,7 @@ struct SolveBufs {
   cd* Y;
   int* nzflag;
   int* nzfirst;  // first grid column of f^l with a non-zero entry
+  cf* chunk_bnd; // chunked local solves: y'_b, x''_a, beta, gamma per (source, layer, chunk)
   cd *b, *x, *w, *t, *u1, *V, *Z, *partial, *coef, *H, *sn, *g, *y;
   double *cs, *resid, *nrm;
   int* kk;
@@ -419,6 +445,7 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
   b.Y = c.take<cd>((size_t)(P.tc ? std::max(S, 16) : S) * P.L * P.nt * P.nloc_max);
   b.nzflag = c.take<int>((size_t)S * P.L);
   b.nzfirst = c.take<int>((size_t)S * P.L);
+  if (P.kr > 0) b.chunk_bnd = c.take<cf>((size_t)S * P.L * std::max(P.kr, P.kv) * 4 * P.nloc_max);
   b.b = c.take<cd>(S * N);
   b.x = c.take<cd>(S * N);
   b.w = c.take<cd>(S * N);
@@ -864,6 +891,7 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   c->P = P;
   c->stream = static_cast<cudaStream_t>(stream);
   c->d = carve_persist(P, prm, persistent, nullptr);
+  if (c->d.chunk_T) c->opt_local_solve = 4;  // mixed FP32: chunked local solves by default
   auto bail = [&](pt_status s) { delete c; return s; };
   cudaStream_t s = c->stream;
   const Geometry& g = P.g;
@@ -901,6 +929,17 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   if (e == cudaSuccess && c->d.sinv_hi) e = launch_split_sinv(c->d.Sinv, P.sinv_elems, c->d.sinv_hi, c->d.sinv_lo, s);
   if (e == cudaSuccess && c->d.w_hi) e = launch_split_sinv(c->d.W, P.coef_elems, c->d.w_hi, c->d.w_lo, s);
   if (e == cudaSuccess && c->d.e_hi) e = launch_split_sinv(c->d.E, P.coef_elems, c->d.e_hi, c->d.e_lo, s);
+  if (e == cudaSuccess && c->d.chunk_T) {  // after the extraction: it reuses the setup scratch
+    e = cudaMemsetAsync(c->d.chunk_T, 0,
+                        ((size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max + 64) * sizeof(cf), s);
+    if (e == cudaSuccess)
+      e = launch_chunk_transfer(g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, P.kr, P.nloc_max, static_cast<cd*>(setup),
+                              c->d.chunk_T, s);
+    if (e == cudaSuccess)
+      e = launch_chunk_transfer(g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, P.kv, P.nloc_max,
+                                static_cast<cd*>(setup),
+                                c->d.chunk_T + (size_t)P.L * P.kr * 3 * P.nloc_max * P.nloc_max, s);
+  }
   if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline launch: ") + cudaGetErrorString(e)));
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(fail(PT_ERR_CUDA, std::string("offline phase: ") + cudaGetErrorString(e)));
@@ -1105,6 +1144,14 @@ cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xt
   }
   if (mixed(c)) {
     if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
+    if (c->opt_local_solve == 4 && c->d.chunk_T && B.chunk_bnd) {  // FP32, chunked along x
+      const int K = mode == 0 ? P.kr : P.kv;
+      const cf* Tm = c->d.chunk_T + (mode == 0 ? 0 : (size_t)P.L * P.kr * 3 * P.nloc_max * P.nloc_max);
+      c->launches += 2;
+      return launch_layer_solve_chunked(mode, P.g, c->d.layers, P.nloc_max, K, Tm, c->d.sinv_hi, c->d.w_hi,
+                                        c->d.e_hi, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag,
+                                        B.chunk_bnd, S, c->d.status, c->stream);
+    }
     if (c->opt_local_solve != 1)  // FP32 on a cluster of 4 (0) or 8 (3) CTAs, or one CTA (2), per (layer, source)
       return launch_layer_solve_f32(mode, P.g, c->d.layers, P.nloc_max, c->d.sinv_hi, c->d.w_hi, c->d.e_hi, f, xtr,
                                     B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag, B.nzfirst, S, c->d.status,
@@ -1190,7 +1237,8 @@ extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
     return PT_OK;
   }
   if (option == PT_OPT_LOCAL_SOLVE) {
-    if (value < 0 || value > 3) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0, 1, 2 or 3");
+    if (value < 0 || value > 4) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0, 1, 2, 3 or 4");
+    if (value == 4 && !ctx->d.chunk_T) return fail(PT_ERR_ARG, "chunked local solves need PT_MIXED_FP32");
     ctx->opt_local_solve = value;
     return PT_OK;
   }
@@ -1617,7 +1665,7 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     PT_CUDA(cudaMemsetAsync(B.H, 0, (size_t)S * (m + 1) * m * sizeof(cd), s));
     PT_CUDA(cudaMemsetAsync(B.g, 0, (size_t)S * (m + 1) * sizeof(cd), s));
     c->launches++;
-    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, B.g, 1, m + 1, 0, 0, B.V, N, s));
+    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, B.g, 1, m + 1, 0, 0, B.V, N, reinterpret_cast<double*>(B.partial), s));
     PT_CUDA(cudaMemcpyAsync(nrm.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
     PT_CUDA(cudaStreamSynchronize(s));
     if (first) {
@@ -1657,7 +1705,8 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
         PT_CUDA(launch_update(B.V, S, N, B.w, j + 1, B.coef, m + 1, s));
       }
       c->launches += 2;
-      PT_CUDA(launch_norm_scale(B.w, N, S, nullptr, B.H, m + 1, m, j + 1, j, B.V + (size_t)(j + 1) * S * N, N, s));
+      PT_CUDA(launch_norm_scale(B.w, N, S, nullptr, B.H, m + 1, m, j + 1, j, B.V + (size_t)(j + 1) * S * N, N,
+                                reinterpret_cast<double*>(B.partial), s));
       PT_CUDA(launch_givens(S, m, j, B.H, B.cs, B.sn, B.g, B.resid, s));
       PT_CUDA(cudaMemcpyAsync(c->resid_h.data(), B.resid, S * sizeof(double), cudaMemcpyDeviceToHost, s));
       PT_CUDA(cudaStreamSynchronize(s));
@@ -1686,7 +1735,8 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     else PT_CUDA(do_matvec(c, S, B.x, B.t));
     c->launches += 2;
     PT_CUDA(launch_sub(B.b, B.t, B.w, S * N, s));
-    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, s));
+    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, reinterpret_cast<double*>(B.partial),
+                              s));
     PT_CUDA(cudaMemcpyAsync(nrm.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
     PT_CUDA(cudaStreamSynchronize(s));
     bool all = true;

@@ -376,8 +376,22 @@ __global__ void __launch_bounds__(256) apply_lowp_kernel(int nt, int ld, int T4,
         const float4* Lo = reinterpret_cast<const float4*>(blocks_b + off);
         const float4* xv = xin + t * ld;
         int k = lane;
+        // the next pair of columns' block values is loaded while the current pair computes
+        float4 nh0, nl0, nh1, nl1;
+        if (k + 32 < np) {
+          nh0 = __ldg(H + k);
+          nl0 = __ldg(Lo + k);
+          nh1 = __ldg(H + k + 32);
+          nl1 = __ldg(Lo + k + 32);
+        }
         for (; k + 32 < np; k += 64) {
-          const float4 h0 = __ldg(H + k), l0 = __ldg(Lo + k), h1 = __ldg(H + k + 32), l1 = __ldg(Lo + k + 32);
+          const float4 h0 = nh0, l0 = nl0, h1 = nh1, l1 = nl1;
+          if (k + 96 < np) {
+            nh0 = __ldg(H + k + 64);
+            nl0 = __ldg(Lo + k + 64);
+            nh1 = __ldg(H + k + 96);
+            nl1 = __ldg(Lo + k + 96);
+          }
           const float4 a0 = xv[2 * k], a1 = xv[2 * k + 1];
           const float4 b0 = xv[2 * (k + 32)], b1 = xv[2 * (k + 32) + 1];
           df_mac(h0.x, l0.x, a0.x, a0.z, Sr, Cr);

@@ -12,7 +12,7 @@ namespace pt {
 // GMRES (FP64).  Basis layout V[j][s][N], N = 4 (L-1) n_t complex entries.
 // ---------------------------------------------------------------------------
 constexpr int kDotThreads = 256;
-constexpr int kDotChunk = 4096;  // entries per CTA
+constexpr int kDotChunk = 1024;  // entries per CTA: the FP64 work of a reduction spread over the SMs
 
 // partial[(s * nvec + j) * nchunks + c] = sum_{k in chunk c} conj(V_j[s][k]) w[s][k]
 __global__ void __launch_bounds__(kDotThreads) dots_kernel(const cd* __restrict__ V, int nsrc, size_t N,
@@ -70,35 +70,63 @@ __global__ void update_kernel(const cd* __restrict__ V, int nsrc, size_t N, cd* 
   }
 }
 
-// nrm[s] = ||w_s||, optional H[s][row][col] = nrm; dst_s = w_s / nrm (0 when nrm ~ 0).  One CTA per source.
-__global__ void __launch_bounds__(1024) norm_scale_kernel(const cd* __restrict__ w, size_t N, double* __restrict__ nrm,
-                                                          cd* __restrict__ H, int hrows, int hcols, int row, int col,
-                                                          cd* __restrict__ dst, size_t dst_stride) {
-  const int s = blockIdx.x;
-  const cd* ws = w + (size_t)s * N;
-  double acc = 0.0;
-  for (size_t k = threadIdx.x; k < N; k += blockDim.x) acc = fma(ws[k].x, ws[k].x, fma(ws[k].y, ws[k].y, acc));
-  __shared__ double red[32];
+// nrm[s] = ||w_s||, optional H[s][row][col] = nrm; dst_s = w_s / nrm (0 when nrm ~ 0).
+// Two passes over chunks of kNormChunk entries: per-chunk sums of squares, then every
+// chunk's CTA forms the same total (the partials summed in a fixed order), and scales
+// its chunk.  A single CTA per source would keep the whole vector's FP64 arithmetic on
+// one SM's FP64 pipe (2 lanes per clock on GB300).
+constexpr int kNormChunk = 1024;
+constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  __shared__ double s_n;
+  double t = 0.0;
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+    t = threadIdx.x < kNormThreads / 32 ? red[threadIdx.x] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) {
-      s_n = sqrt(v);
-      if (nrm) nrm[s] = s_n;
-      if (H) H[((size_t)s * hrows + row) * hcols + col] = make_double2(s_n, 0.0);
-    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[0] = t;
   }
   __syncthreads();
+  t = red[0];
+  __syncthreads();  // red is reused by the caller's next reduction
+  return t;
+}
+
+__global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(const cd* __restrict__ w, size_t N, int nb,
+                                                                     double* __restrict__ part) {
+  const int b = blockIdx.x, s = blockIdx.y;
+  const cd* ws = w + (size_t)s * N;
+  const size_t k0 = (size_t)b * kNormChunk, k1 = min(N, k0 + kNormChunk);
+  double acc = 0.0;
+  for (size_t k = k0 + threadIdx.x; k < k1; k += kNormThreads) acc = fma(ws[k].x, ws[k].x, fma(ws[k].y, ws[k].y, acc));
+  __shared__ double red[32];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(size_t)s * nb + b] = acc;
+}
+
+__global__ void __launch_bounds__(kNormThreads) norm_finish_kernel(const cd* __restrict__ w, size_t N, int nb,
+                                                                    const double* __restrict__ part,
+                                                                    double* __restrict__ nrm, cd* __restrict__ H,
+                                                                    int hrows, int hcols, int row, int col,
+                                                                    cd* __restrict__ dst, size_t dst_stride) {
+  const int b = blockIdx.x, s = blockIdx.y;
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < nb; c += kNormThreads) acc += part[(size_t)s * nb + c];
+  __shared__ double red[32];
+  const double nv = sqrt(block_sum(acc, red));
+  if (b == 0 && threadIdx.x == 0) {
+    if (nrm) nrm[s] = nv;
+    if (H) H[((size_t)s * hrows + row) * hcols + col] = make_double2(nv, 0.0);
+  }
   if (dst) {
-    const double nv = s_n;
     const double inv = nv > 1e-300 ? 1.0 / nv : 0.0;
-    for (size_t k = threadIdx.x; k < N; k += blockDim.x) dst[(size_t)s * dst_stride + k] = cscale(ws[k], inv);
+    const cd* ws = w + (size_t)s * N;
+    const size_t k0 = (size_t)b * kNormChunk, k1 = min(N, k0 + kNormChunk);
+    for (size_t k = k0 + threadIdx.x; k < k1; k += kNormThreads) dst[(size_t)s * dst_stride + k] = cscale(ws[k], inv);
   }
 }
 
@@ -275,14 +303,18 @@ cudaError_t launch_dots(const cd* V, int nsrc, size_t N, const cd* w, int nvec, 
 
 cudaError_t launch_update(const cd* V, int nsrc, size_t N, cd* w, int nvec, const cd* coef, int coef_stride,
                           cudaStream_t s) {
-  int gx = (int)std::min<size_t>((N + 1023) / 1024, 1024);
+  int gx = (int)std::min<size_t>((N + 255) / 256, 4096);  // one entry per thread: the FP64 updates on every SM
   update_kernel<<<dim3(gx, nsrc), 256, 0, s>>>(V, nsrc, N, w, nvec, coef, coef_stride);
   return cudaGetLastError();
 }
 
+// part: scratch of nsrc * ceil(N / kNormChunk) doubles
 cudaError_t launch_norm_scale(const cd* w, size_t N, int nsrc, double* nrm, cd* H, int hrows, int hcols, int row,
-                              int col, cd* dst, size_t dst_stride, cudaStream_t s) {
-  norm_scale_kernel<<<nsrc, 1024, 0, s>>>(w, N, nrm, H, hrows, hcols, row, col, dst, dst_stride);
+                              int col, cd* dst, size_t dst_stride, double* part, cudaStream_t s) {
+  const int nb = (int)((N + kNormChunk - 1) / kNormChunk);
+  norm_partial_kernel<<<dim3(nb, nsrc), kNormThreads, 0, s>>>(w, N, nb, part);
+  norm_finish_kernel<<<dim3(dst ? nb : 1, nsrc), kNormThreads, 0, s>>>(w, N, nb, part, nrm, H, hrows, hcols, row, col,
+                                                                       dst, dst_stride);
   return cudaGetLastError();
 }
 
