@@ -354,7 +354,7 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
   if (p->precision == PT_MIXED_FP32 && !P.plr) q.sweep_y32 = c.take<cf>((size_t)p->max_sources * P.T4 * P.nt);
   if (p->precision != PT_FP64 && !P.plr) q.xprep = c.take<float4>((size_t)p->max_sources * P.T4 * P.ld32);
   if (P.kr > 0)
-    q.chunk_T = c.take<cf>((size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max + 64);  // + read slack
+    q.chunk_T = c.take<cf>((size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max);
   q.tab_matvec = c.take<ApplyRow>(P.T4);
   q.tab_R = c.take<ApplyRow>(P.T4);
   q.tab_sweep = c.take<ApplyRow>((size_t)(P.L - 1) * 4);
@@ -930,8 +930,7 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   if (e == cudaSuccess && c->d.w_hi) e = launch_split_sinv(c->d.W, P.coef_elems, c->d.w_hi, c->d.w_lo, s);
   if (e == cudaSuccess && c->d.e_hi) e = launch_split_sinv(c->d.E, P.coef_elems, c->d.e_hi, c->d.e_lo, s);
   if (e == cudaSuccess && c->d.chunk_T) {  // after the extraction: it reuses the setup scratch
-    e = cudaMemsetAsync(c->d.chunk_T, 0,
-                        ((size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max + 64) * sizeof(cf), s);
+    e = cudaMemsetAsync(c->d.chunk_T, 0, (size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max * sizeof(cf), s);
     if (e == cudaSuccess)
       e = launch_chunk_transfer(g, c->d.layers, c->d.Sinv, c->d.W, c->d.E, P.kr, P.nloc_max, static_cast<cd*>(setup),
                               c->d.chunk_T, s);

@@ -364,13 +364,15 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
 
 // ---- phase 2: the chunk boundary values of each (layer, source) ---------------------
 // beta_0 = 0, beta_{k+1} = y'_{b_k} + Phi_k beta_k;  gamma_{K-1} = 0,
-// gamma_{k-1} = x''_{a_k} + M_k beta_k + Psi_k gamma_k.  Four threads per row; every
-// matrix of the layer is requested into L2 when the CTA starts, and a thread issues all
-// loads of its row quarter at once (one L2 round trip per product); the betas are kept
-// in shared memory.
+// gamma_{k-1} = x''_{a_k} + M_k beta_k + Psi_k gamma_k.  Warp w owns rows w, w + 16, ...;
+// its lanes read a row's columns lane, lane + 32, ... (coalesced), all rows of a product
+// in flight at once (one round trip per matrix), the vector held in registers; the
+// betas and the phase-1 boundary values stay in shared memory.  Every matrix of the layer is requested into L2 when the
+// CTA starts.
 constexpr int kPropThreads = 512;
-constexpr int kPropPer = (kMaxNloc + 3) / 4;  // row entries per thread
-constexpr int kPropHalf = (kPropPer + 1) / 2;
+constexpr int kPropWarps = kPropThreads / 32;
+constexpr int kPropRows = (kMaxNloc + kPropWarps - 1) / kPropWarps;  // rows per warp
+constexpr int kPropCols = (kMaxNloc + 31) / 32;                      // columns per lane
 
 __global__ void __launch_bounds__(kPropThreads)
     chunk_propagate_kernel(Geometry g, const LayerInfo* __restrict__ layers, int K, int nmax,
@@ -381,20 +383,23 @@ __global__ void __launch_bounds__(kPropThreads)
   if (mode == 0 && nzflag[s * g.L + l] == 0) return;
   cf* beta = reinterpret_cast<cf*>(smem);  // [K][nmax]
   cf* gam = beta + (size_t)K * nmax;       // [nmax]
+  cf* yb = gam + nmax;                     // [K][nmax]: y'_{b_k}
+  cf* xa = yb + (size_t)K * nmax;          // [K][nmax]: x''_{a_k}
   const size_t slot = (size_t)nmax * nmax;
   cf* bl = bnd + ((size_t)s * g.L + l) * K * 4 * nmax;
   const cf* Tl = Tm + (size_t)l * K * 3 * slot;
+  for (int i = threadIdx.x; i < K * n; i += blockDim.x) {  // the phase-1 boundary values, off the chain
+    const int k = i / n, r = i - k * n;
+    yb[(size_t)k * nmax + r] = bl[((size_t)k * 4 + 0) * nmax + r];
+    xa[(size_t)k * nmax + r] = bl[((size_t)k * 4 + 1) * nmax + r];
+  }
   for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) {  // L2 prefetch hints, 16-byte aligned parts
     const uintptr_t p0 = reinterpret_cast<uintptr_t>(Tl + (size_t)i * slot);
     const uintptr_t a0 = (p0 + 15) & ~(uintptr_t)15, a1 = (p0 + (size_t)n * n * sizeof(cf)) & ~(uintptr_t)15;
     if (a1 > a0)
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
   }
-  const int r = threadIdx.x / 4, q = threadIdx.x % 4;
-  const bool own = r < n && q == 0;
-  const int per = (n + 3) / 4;
-  const int c0 = q * per, cnt = max(0, min(n, c0 + per) - c0);
-  const int rr = min(r, n - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < nmax; i += blockDim.x) {
     beta[i] = make_float2(0.f, 0.f);
     gam[i] = make_float2(0.f, 0.f);
@@ -402,65 +407,77 @@ __global__ void __launch_bounds__(kPropThreads)
     bl[((size_t)(K - 1) * 4 + 3) * nmax + i] = make_float2(0.f, 0.f);  // gamma_{K-1}
   }
   __syncthreads();
-  // (sr, si) += row rr, columns [c0, c0 + cnt) of A times v: two halves, all loads of a half
-  // in flight together.  A quarter row reads up to kPropPer entries from c0: past the row's
-  // end it reads the next row (or the slack behind the matrices and behind the vectors in
-  // shared memory), and those terms are dropped.
-  auto dot = [&](const cf* A, const cf* v, float& sr, float& si) {
-    const cf* row = A + (size_t)rr * n + c0;
-    const cf* xv = v + c0;
+  // acc[i] += row (warp + 16 i) of A times v, the sum over the warp's lanes left in every lane
+  auto gemv = [&](const cf* A, const cf* v, float2 (&acc)[kPropRows]) {
+    cf xr[kPropCols];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      cf m[kPropHalf];
+    for (int c = 0; c < kPropCols; ++c) {
+      const int col = lane + 32 * c;
+      xr[c] = col < n ? v[col] : make_float2(0.f, 0.f);
+    }
+    cf m[kPropRows][kPropCols];
 #pragma unroll
-      for (int u = 0; u < kPropHalf; ++u) m[u] = __ldg(row + h * kPropHalf + u);
+    for (int i = 0; i < kPropRows; ++i) {
+      const int row = warp + kPropWarps * i;
 #pragma unroll
-      for (int u = 0; u < kPropHalf; ++u) {
-        const int uu = h * kPropHalf + u;
-        const bool in = uu < cnt;  // a select, not a 0 weight: the surplus reads may hold anything
-        const cf x = in ? xv[uu] : make_float2(0.f, 0.f);
-        const float mx = in ? m[u].x : 0.f, my = in ? m[u].y : 0.f;
-        sr = fmaf(mx, x.x, sr);
-        sr = fmaf(-my, x.y, sr);
-        si = fmaf(mx, x.y, si);
-        si = fmaf(my, x.x, si);
+      for (int c = 0; c < kPropCols; ++c) {
+        const int col = lane + 32 * c;
+        m[i][c] = (row < n && col < n) ? __ldg(A + (size_t)row * n + col) : make_float2(0.f, 0.f);
       }
-      asm volatile("" ::: "memory");  // one half's loads in flight at a time (registers)
+    }
+#pragma unroll
+    for (int i = 0; i < kPropRows; ++i) {
+      float sr = 0.f, si = 0.f;
+#pragma unroll
+      for (int c = 0; c < kPropCols; ++c) {
+        sr = fmaf(m[i][c].x, xr[c].x, sr);
+        sr = fmaf(-m[i][c].y, xr[c].y, sr);
+        si = fmaf(m[i][c].x, xr[c].y, si);
+        si = fmaf(m[i][c].y, xr[c].x, si);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      acc[i].x += sr;
+      acc[i].y += si;
     }
   };
-  auto reduce4 = [&](float& sr, float& si) {
-    sr += __shfl_xor_sync(0xffffffffu, sr, 1);
-    si += __shfl_xor_sync(0xffffffffu, si, 1);
-    sr += __shfl_xor_sync(0xffffffffu, sr, 2);
-    si += __shfl_xor_sync(0xffffffffu, si, 2);
-  };
   for (int k = 0; k + 1 < K; ++k) {
-    float sr = 0.f, si = 0.f;
-    dot(Tl + (size_t)k * 3 * slot, beta + (size_t)k * nmax, sr, si);
-    reduce4(sr, si);
-    if (own) {
-      const cf y = bl[((size_t)k * 4 + 0) * nmax + r];
-      const cf v = make_float2(y.x + sr, y.y + si);
-      beta[(size_t)(k + 1) * nmax + r] = v;
-      bl[((size_t)(k + 1) * 4 + 2) * nmax + r] = v;
+    float2 acc[kPropRows];
+#pragma unroll
+    for (int i = 0; i < kPropRows; ++i) acc[i] = make_float2(0.f, 0.f);
+    gemv(Tl + (size_t)k * 3 * slot, beta + (size_t)k * nmax, acc);
+#pragma unroll
+    for (int i = 0; i < kPropRows; ++i) {
+      const int row = warp + kPropWarps * i;
+      if (lane == 0 && row < n) {
+        const cf y = yb[(size_t)k * nmax + row];
+        const cf v = make_float2(y.x + acc[i].x, y.y + acc[i].y);
+        beta[(size_t)(k + 1) * nmax + row] = v;
+        bl[((size_t)(k + 1) * 4 + 2) * nmax + row] = v;
+      }
     }
     __syncthreads();
   }
   for (int k = K - 1; k >= 1; --k) {
-    float sr = 0.f, si = 0.f;
-    dot(Tl + ((size_t)k * 3 + 1) * slot, beta + (size_t)k * nmax, sr, si);
+    float2 acc[kPropRows];
+#pragma unroll
+    for (int i = 0; i < kPropRows; ++i) acc[i] = make_float2(0.f, 0.f);
+    gemv(Tl + ((size_t)k * 3 + 1) * slot, beta + (size_t)k * nmax, acc);
     asm volatile("" ::: "memory");  // one matrix's loads in flight at a time (registers)
-    dot(Tl + ((size_t)k * 3 + 2) * slot, gam, sr, si);
-    reduce4(sr, si);
-    cf v = make_float2(0.f, 0.f);
-    if (own) {
-      const cf x = bl[((size_t)k * 4 + 1) * nmax + r];
-      v = make_float2(x.x + sr, x.y + si);
-    }
-    __syncthreads();  // every thread has read gamma_k
-    if (own) {
-      gam[r] = v;
-      bl[((size_t)(k - 1) * 4 + 3) * nmax + r] = v;
+    gemv(Tl + ((size_t)k * 3 + 2) * slot, gam, acc);
+    __syncthreads();  // every warp has read gamma_k
+#pragma unroll
+    for (int i = 0; i < kPropRows; ++i) {
+      const int row = warp + kPropWarps * i;
+      if (lane == 0 && row < n) {
+        const cf x = xa[(size_t)k * nmax + row];
+        const cf v = make_float2(x.x + acc[i].x, x.y + acc[i].y);
+        gam[row] = v;
+        bl[((size_t)(k - 1) * 4 + 3) * nmax + row] = v;
+      }
     }
     __syncthreads();
   }
@@ -488,7 +505,7 @@ cudaError_t launch_layer_solve_chunked(int mode, const Geometry& g, const LayerI
     e = mode == 0 ? go(layer_solve_chunk_kernel<0, 1>) : go(layer_solve_chunk_kernel<1, 1>);
     if (e != cudaSuccess) return e;
   }
-  const size_t psmem = (((size_t)K + 1) * nloc_max + 2 * kPropPer) * sizeof(cf);
+  const size_t psmem = ((size_t)3 * K + 1) * nloc_max * sizeof(cf);
   e = smem_limit_max(reinterpret_cast<const void*>(chunk_propagate_kernel));
   if (e != cudaSuccess) return e;
   chunk_propagate_kernel<<<dim3(g.L, nsrc), kPropThreads, psmem, s>>>(g, layers, K, nloc_max, Tm, flag, mode, bnd);
