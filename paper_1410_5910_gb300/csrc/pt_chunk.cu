@@ -364,19 +364,20 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
 
 // ---- phase 2: the chunk boundary values of each (layer, source) ---------------------
 // beta_0 = 0, beta_{k+1} = y'_{b_k} + Phi_k beta_k;  gamma_{K-1} = 0,
-// gamma_{k-1} = x''_{a_k} + M_k beta_k + Psi_k gamma_k.  Warp w owns rows w, w + 16, ...;
-// its lanes read a row's columns lane, lane + 32, ... (coalesced), all rows of a product
-// in flight at once (one round trip per matrix), the vector held in registers; the
-// betas and the phase-1 boundary values stay in shared memory.  Every matrix of the layer is requested into L2 when the
-// CTA starts.
+// gamma_{k-1} = x''_{a_k} + M_k beta_k + Psi_k gamma_k.  Warp w owns rows w + 16 j
+// (j < 8); lane (rg, cg) = (lane / 8, lane % 8) takes rows j = rg, rg + 4 and the columns
+// cg + 8 u, so eight lanes read 64 contiguous bytes of a row, a product is one round trip
+// (every load of the lane in flight), and a row sum needs three shuffles.  The vector is
+// held in registers; the betas and the phase-1 boundary values stay in shared memory;
+// every matrix of the layer is requested into L2 when the CTA starts.
 constexpr int kPropThreads = 512;
 constexpr int kPropWarps = kPropThreads / 32;
-constexpr int kPropRows = (kMaxNloc + kPropWarps - 1) / kPropWarps;  // rows per warp
-constexpr int kPropCols = (kMaxNloc + 31) / 32;                      // columns per lane
+constexpr int kPropCols = (kMaxNloc + 7) / 8;  // columns per lane
 
 __global__ void __launch_bounds__(kPropThreads)
     chunk_propagate_kernel(Geometry g, const LayerInfo* __restrict__ layers, int K, int nmax,
                            const cf* __restrict__ Tm, const int* __restrict__ nzflag, int mode, cf* __restrict__ bnd) {
+  static_assert(kPropWarps * 8 >= kMaxNloc, "eight rows per warp cover a local problem");
   extern __shared__ __align__(16) unsigned char smem[];
   const int l = blockIdx.x, s = blockIdx.y;
   const int n = layers[l].nloc;
@@ -400,6 +401,8 @@ __global__ void __launch_bounds__(kPropThreads)
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rg = lane >> 3, cg = lane & 7;
+  const int row0 = warp + kPropWarps * rg, row1 = warp + kPropWarps * (rg + 4);
   for (int i = threadIdx.x; i < nmax; i += blockDim.x) {
     beta[i] = make_float2(0.f, 0.f);
     gam[i] = make_float2(0.f, 0.f);
@@ -407,76 +410,77 @@ __global__ void __launch_bounds__(kPropThreads)
     bl[((size_t)(K - 1) * 4 + 3) * nmax + i] = make_float2(0.f, 0.f);  // gamma_{K-1}
   }
   __syncthreads();
-  // acc[i] += row (warp + 16 i) of A times v, the sum over the warp's lanes left in every lane
-  auto gemv = [&](const cf* A, const cf* v, float2 (&acc)[kPropRows]) {
-    cf xr[kPropCols];
+  // acc0 / acc1 += rows row0 / row1 of A times v, summed over the eight lanes of the row group
+  auto gemv = [&](const cf* A, const cf* v, float2& acc0, float2& acc1) {
+    cf xr[kPropCols], m0[kPropCols], m1[kPropCols];
 #pragma unroll
-    for (int c = 0; c < kPropCols; ++c) {
-      const int col = lane + 32 * c;
-      xr[c] = col < n ? v[col] : make_float2(0.f, 0.f);
+    for (int u = 0; u < kPropCols; ++u) {
+      const int col = cg + 8 * u;
+      xr[u] = col < n ? v[col] : make_float2(0.f, 0.f);
+      m0[u] = (row0 < n && col < n) ? __ldg(A + (size_t)row0 * n + col) : make_float2(0.f, 0.f);
+      m1[u] = (row1 < n && col < n) ? __ldg(A + (size_t)row1 * n + col) : make_float2(0.f, 0.f);
     }
-    cf m[kPropRows][kPropCols];
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
-    for (int i = 0; i < kPropRows; ++i) {
-      const int row = warp + kPropWarps * i;
-#pragma unroll
-      for (int c = 0; c < kPropCols; ++c) {
-        const int col = lane + 32 * c;
-        m[i][c] = (row < n && col < n) ? __ldg(A + (size_t)row * n + col) : make_float2(0.f, 0.f);
-      }
+    for (int u = 0; u < kPropCols; ++u) {
+      ar = fmaf(m0[u].x, xr[u].x, ar);
+      ar = fmaf(-m0[u].y, xr[u].y, ar);
+      ai = fmaf(m0[u].x, xr[u].y, ai);
+      ai = fmaf(m0[u].y, xr[u].x, ai);
+      br = fmaf(m1[u].x, xr[u].x, br);
+      br = fmaf(-m1[u].y, xr[u].y, br);
+      bi = fmaf(m1[u].x, xr[u].y, bi);
+      bi = fmaf(m1[u].y, xr[u].x, bi);
     }
 #pragma unroll
-    for (int i = 0; i < kPropRows; ++i) {
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int c = 0; c < kPropCols; ++c) {
-        sr = fmaf(m[i][c].x, xr[c].x, sr);
-        sr = fmaf(-m[i][c].y, xr[c].y, sr);
-        si = fmaf(m[i][c].x, xr[c].y, si);
-        si = fmaf(m[i][c].y, xr[c].x, si);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
-      }
-      acc[i].x += sr;
-      acc[i].y += si;
+    for (int o = 1; o < 8; o <<= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+      br += __shfl_xor_sync(0xffffffffu, br, o);
+      bi += __shfl_xor_sync(0xffffffffu, bi, o);
     }
+    acc0.x += ar;
+    acc0.y += ai;
+    acc1.x += br;
+    acc1.y += bi;
   };
   for (int k = 0; k + 1 < K; ++k) {
-    float2 acc[kPropRows];
-#pragma unroll
-    for (int i = 0; i < kPropRows; ++i) acc[i] = make_float2(0.f, 0.f);
-    gemv(Tl + (size_t)k * 3 * slot, beta + (size_t)k * nmax, acc);
-#pragma unroll
-    for (int i = 0; i < kPropRows; ++i) {
-      const int row = warp + kPropWarps * i;
-      if (lane == 0 && row < n) {
-        const cf y = yb[(size_t)k * nmax + row];
-        const cf v = make_float2(y.x + acc[i].x, y.y + acc[i].y);
-        beta[(size_t)(k + 1) * nmax + row] = v;
-        bl[((size_t)(k + 1) * 4 + 2) * nmax + row] = v;
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+    gemv(Tl + (size_t)k * 3 * slot, beta + (size_t)k * nmax, a0, a1);
+    if (cg == 0) {
+      if (row0 < n) {
+        const cf y = yb[(size_t)k * nmax + row0];
+        const cf v = make_float2(y.x + a0.x, y.y + a0.y);
+        beta[(size_t)(k + 1) * nmax + row0] = v;
+        bl[((size_t)(k + 1) * 4 + 2) * nmax + row0] = v;
+      }
+      if (row1 < n) {
+        const cf y = yb[(size_t)k * nmax + row1];
+        const cf v = make_float2(y.x + a1.x, y.y + a1.y);
+        beta[(size_t)(k + 1) * nmax + row1] = v;
+        bl[((size_t)(k + 1) * 4 + 2) * nmax + row1] = v;
       }
     }
     __syncthreads();
   }
   for (int k = K - 1; k >= 1; --k) {
-    float2 acc[kPropRows];
-#pragma unroll
-    for (int i = 0; i < kPropRows; ++i) acc[i] = make_float2(0.f, 0.f);
-    gemv(Tl + ((size_t)k * 3 + 1) * slot, beta + (size_t)k * nmax, acc);
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+    gemv(Tl + ((size_t)k * 3 + 1) * slot, beta + (size_t)k * nmax, a0, a1);
     asm volatile("" ::: "memory");  // one matrix's loads in flight at a time (registers)
-    gemv(Tl + ((size_t)k * 3 + 2) * slot, gam, acc);
+    gemv(Tl + ((size_t)k * 3 + 2) * slot, gam, a0, a1);
     __syncthreads();  // every warp has read gamma_k
-#pragma unroll
-    for (int i = 0; i < kPropRows; ++i) {
-      const int row = warp + kPropWarps * i;
-      if (lane == 0 && row < n) {
-        const cf x = xa[(size_t)k * nmax + row];
-        const cf v = make_float2(x.x + acc[i].x, x.y + acc[i].y);
-        gam[row] = v;
-        bl[((size_t)(k - 1) * 4 + 3) * nmax + row] = v;
+    if (cg == 0) {
+      if (row0 < n) {
+        const cf x = xa[(size_t)k * nmax + row0];
+        const cf v = make_float2(x.x + a0.x, x.y + a0.y);
+        gam[row0] = v;
+        bl[((size_t)(k - 1) * 4 + 3) * nmax + row0] = v;
+      }
+      if (row1 < n) {
+        const cf x = xa[(size_t)k * nmax + row1];
+        const cf v = make_float2(x.x + a1.x, x.y + a1.y);
+        gam[row1] = v;
+        bl[((size_t)(k - 1) * 4 + 3) * nmax + row1] = v;
       }
     }
     __syncthreads();

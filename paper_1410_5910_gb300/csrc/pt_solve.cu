@@ -1034,18 +1034,34 @@ cudaError_t launch_layer_solve_f32(int mode, const Geometry& g, const LayerInfo*
 }
 
 // flag[s * L + l] = 1 when f^l of source s has a non-zero entry; first (optional) = the
-// first grid column with one (n_t when none): the forward substitution is zero before it
-__global__ void layer_nonzero_kernel(Geometry g, const LayerInfo* __restrict__ layers, const cd* __restrict__ f,
-                                     int* __restrict__ flag, int* __restrict__ first) {
+// first grid column with one (n_t when none): the forward substitution is zero before it.
+// 1024 threads, eight loads in flight per thread (a layer of the 511 x 1023 workload is
+// 36 K entries: about five round trips).
+constexpr int kNzThreads = 1024;
+constexpr int kNzUnroll = 8;
+
+__global__ void __launch_bounds__(kNzThreads) layer_nonzero_kernel(Geometry g, const LayerInfo* __restrict__ layers,
+                                                                   const cd* __restrict__ f, int* __restrict__ flag,
+                                                                   int* __restrict__ first) {
   const LayerInfo L = layers[blockIdx.x];
   const int s = blockIdx.y;
   const cd* fs = f + (size_t)s * g.Nz * g.nt + (size_t)L.start * g.nt;
+  const size_t total = (size_t)L.n * g.nt;
   int nz = 0, fc = g.nt;
-  for (size_t k = threadIdx.x; k < (size_t)L.n * g.nt; k += blockDim.x) {
-    cd v = fs[k];
-    if (v.x != 0.0 || v.y != 0.0) {
-      nz = 1;
-      fc = min(fc, (int)(k % g.nt));
+  for (size_t base = 0; base < total; base += (size_t)kNzThreads * kNzUnroll) {
+    cd v[kNzUnroll];
+#pragma unroll
+    for (int u = 0; u < kNzUnroll; ++u) {
+      const size_t k = base + (size_t)u * kNzThreads + threadIdx.x;
+      v[u] = k < total ? __ldg(fs + k) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < kNzUnroll; ++u) {
+      const size_t k = base + (size_t)u * kNzThreads + threadIdx.x;
+      if (v[u].x != 0.0 || v[u].y != 0.0) {
+        nz = 1;
+        fc = min(fc, (int)(k % g.nt));
+      }
     }
   }
   nz = __syncthreads_or(nz);
@@ -1071,7 +1087,7 @@ __global__ void split_sinv_kernel(const cd* __restrict__ src, size_t n, cf* __re
 
 cudaError_t launch_layer_nonzero(const Geometry& g, const LayerInfo* layers, const cd* f, int* flag, int* first,
                                  int nsrc, cudaStream_t s) {
-  layer_nonzero_kernel<<<dim3(g.L, nsrc), 256, 0, s>>>(g, layers, f, flag, first);
+  layer_nonzero_kernel<<<dim3(g.L, nsrc), kNzThreads, 0, s>>>(g, layers, f, flag, first);
   return cudaGetLastError();
 }
 
