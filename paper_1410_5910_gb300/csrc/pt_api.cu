@@ -86,9 +86,10 @@ bool launch_apply_f32_rows(int, int, int, const ApplyRow*, int, const void*, con
 size_t chunk_work_bytes(int, int, int);
 cudaError_t launch_chunk_transfer(const Geometry&, const LayerInfo*, const cd*, const cd*, const cd*, int, int, cd*,
                                   cf*, cudaStream_t);
+cudaError_t launch_to_c64(const cd*, size_t, cf*, cudaStream_t);
 cudaError_t launch_layer_solve_chunked(int, const Geometry&, const LayerInfo*, int, int, const cf*, const cf*,
-                                       const cf*, const cf*, const cd*, const cd*, cd*, size_t, cd*, const int*, cf*,
-                                       int, int*, cudaStream_t);
+                                       const cf*, const cf*, const cf*, const cd*, cf*, cd*, size_t, cd*, cf*,
+                                       const int*, cf*, int, int*, cudaStream_t);
 cudaError_t launch_prep_inputs(const cd*, int, int, int, bool, void*, cudaStream_t);
 cudaError_t launch_apply_lowp(int, int, int, int, const ApplyRow*, int, const cf*, const cf*, const void*, const cd*,
                               const cd*, cd*, int, int, double, double, cudaStream_t);
@@ -423,6 +424,7 @@ struct SolveBufs {
   int* nzflag;
   int* nzfirst;  // first grid column of f^l with a non-zero entry
   cf* chunk_bnd; // chunked local solves: y'_b, x''_a, beta, gamma per (source, layer, chunk)
+  cf *f32, *tr32, *vol32;  // chunked local solves: complex64 sources, trace forcing and volume
   cd *b, *x, *w, *t, *u1, *V, *Z, *partial, *coef, *H, *sn, *g, *y;
   double *cs, *resid, *nrm;
   int* kk;
@@ -445,7 +447,12 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
   b.Y = c.take<cd>((size_t)(P.tc ? std::max(S, 16) : S) * P.L * P.nt * P.nloc_max);
   b.nzflag = c.take<int>((size_t)S * P.L);
   b.nzfirst = c.take<int>((size_t)S * P.L);
-  if (P.kr > 0) b.chunk_bnd = c.take<cf>((size_t)S * P.L * std::max(P.kr, P.kv) * 4 * P.nloc_max);
+  if (P.kr > 0) {
+    b.chunk_bnd = c.take<cf>((size_t)S * P.L * std::max(P.kr, P.kv) * 4 * P.nloc_max);
+    b.f32 = c.take<cf>((size_t)S * P.Nz * P.nt);
+    b.tr32 = c.take<cf>((size_t)S * P.N);
+    b.vol32 = c.take<cf>((size_t)S * P.Nz * P.nt);
+  }
   b.b = c.take<cd>(S * N);
   b.x = c.take<cd>(S * N);
   b.w = c.take<cd>(S * N);
@@ -1143,13 +1150,17 @@ cudaError_t do_layer_solve(pt_ctx* c, int mode, int S, const cd* f, const cd* xt
   }
   if (mixed(c)) {
     if (!c->d.sinv_hi || !c->d.w_hi || !c->d.e_hi) return cudaErrorInvalidValue;  // never launch on missing factors
-    if (c->opt_local_solve == 4 && c->d.chunk_T && B.chunk_bnd) {  // FP32, chunked along x
+    if (c->opt_local_solve == 4 && c->d.chunk_T && B.chunk_bnd && B.f32) {  // FP32, chunked along x
       const int K = mode == 0 ? P.kr : P.kv;
       const cf* Tm = c->d.chunk_T + (mode == 0 ? 0 : (size_t)P.L * P.kr * 3 * P.nloc_max * P.nloc_max);
-      c->launches += 2;
+      // conversions (sources; for the volume also the traces and the result), phase 1 (K > 1),
+      // propagation, phase 3; one of them is counted on entry
+      c->launches += (mode == 1 ? 3 : 1) + (K > 1 ? 1 : 0) + 2 - 1;
+      cudaError_t e = launch_to_c64(f, (size_t)S * P.Nz * P.nt, B.f32, c->stream);
+      if (e != cudaSuccess) return e;
       return launch_layer_solve_chunked(mode, P.g, c->d.layers, P.nloc_max, K, Tm, c->d.sinv_hi, c->d.w_hi,
-                                        c->d.e_hi, f, xtr, B.Y, (size_t)P.nt * P.nloc_max, out, B.nzflag,
-                                        B.chunk_bnd, S, c->d.status, c->stream);
+                                        c->d.e_hi, B.f32, xtr, B.tr32, B.Y, (size_t)P.nt * P.nloc_max, out, B.vol32,
+                                        B.nzflag, B.chunk_bnd, S, c->d.status, c->stream);
     }
     if (c->opt_local_solve != 1)  // FP32 on a cluster of 4 (0) or 8 (3) CTAs, or one CTA (2), per (layer, source)
       return launch_layer_solve_f32(mode, P.g, c->d.layers, P.nloc_max, c->d.sinv_hi, c->d.w_hi, c->d.e_hi, f, xtr,

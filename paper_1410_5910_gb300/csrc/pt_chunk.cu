@@ -19,6 +19,8 @@
 // complex64).
 #include "pt_common.cuh"
 
+#include <algorithm>
+
 namespace pt {
 
 // ---- offline: Phi_k, M_k, Psi_k of every (layer, chunk), FP64 -----------------------
@@ -128,7 +130,10 @@ cudaError_t launch_chunk_transfer(const Geometry& g, const LayerInfo* layers, co
 // threads per row.  PHASE 1 starts both substitutions from zero and keeps y'_{b_k}
 // and x''_{a_k} (bnd slots 0 and 1); PHASE 3 starts from beta_k, gamma_k (slots 2, 3)
 // and emits: MODE 0 the chunk's part of the right-hand side traces, MODE 1 its columns
-// of the volume.
+// of the volume (complex64; converted to FP64 by a separate pass).  The source and the
+// trace forcing arrive in complex64 as well (converted once per solve): no FP64
+// instruction, which holds the SM's FP64 pipe for 16 cycles per warp on GB300, is left
+// in the column steps.
 constexpr int kChunkThreads = 512;
 constexpr int kChunkQ = 4;  // threads per row
 
@@ -161,9 +166,10 @@ size_t chunk_solve_smem(int nmax) { return (2 * chunk_buf_elems(nmax) + (size_t)
 template <int MODE, int PHASE>
 __global__ void __launch_bounds__(kChunkThreads, 1)
     layer_solve_chunk_kernel(Geometry g, const LayerInfo* __restrict__ layers, int K, const cf* __restrict__ Shi,
-                             const cf* __restrict__ Whi, const cf* __restrict__ Ehi, const cd* __restrict__ f,
-                             const cd* __restrict__ xtr, cf* __restrict__ Ystore, size_t ystride,
-                             cd* __restrict__ out, const int* __restrict__ nzflag, int nmax, cf* __restrict__ bnd,
+                             const cf* __restrict__ Whi, const cf* __restrict__ Ehi, const cf* __restrict__ f,
+                             const cf* __restrict__ xtr, cf* __restrict__ Ystore, size_t ystride,
+                             cd* __restrict__ out, cf* __restrict__ vol, const int* __restrict__ nzflag, int nmax,
+                             cf* __restrict__ bnd,
                              int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -201,8 +207,8 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
   const bool own = r < n && q == 0;  // owner of row r's chain state
   const int per = (n + kChunkQ - 1) / kChunkQ;
   const int k0 = q * per, k1 = min(n, k0 + per);
-  const cd* fs = f + (size_t)s * g.Nz * nt;
-  const cd* xs = (MODE == 1) ? xtr + (size_t)s * T4n : nullptr;
+  const cf* fs = f + (size_t)s * g.Nz * nt;
+  const cf* xs = (MODE == 1) ? xtr + (size_t)s * T4n : nullptr;
   cf* Y = Ystore + ((size_t)s * g.L + l) * ystride;
   const int nsteps = 2 * len;
   auto col = [&](int st) { return st < len ? a + st : b - (st - len); };
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
   };
   // per-row operands of a step, prefetched one step ahead by the row owner
   cf c_next = make_float2(0.f, 0.f), y_next = make_float2(0.f, 0.f);
-  cd f_next = make_double2(0, 0), ta_next = make_double2(0, 0), tb_next = make_double2(0, 0);
+  cf f_next = make_float2(0.f, 0.f), ta_next = make_float2(0.f, 0.f), tb_next = make_float2(0.f, 0.f);
   auto prefetch = [&](int st) {
     if (!own) return;
     const int i = col(st);
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
     const bool edge = fwd ? i == 0 : i == nt - 1;
     c_next = edge ? make_float2(0.f, 0.f) : __ldg((fwd ? Whi : Ehi) + L.coef_off + (size_t)i * n + r);
     if (fwd) {
-      cd v = make_double2(0, 0);
+      cf v = make_float2(0.f, 0.f);
       if (fnz && in_layer) v = fs[frow + i];
       f_next = v;
       if (MODE == 1 && ftr >= 0) {
@@ -298,16 +304,19 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
       chain = PHASE == 3 ? bk[3 * nmax + r] : make_float2(0.f, 0.f);
     }
     const cf c = c_next;
-    const cd fv = f_next, ta = ta_next, tb = tb_next;
+    const cf fv = f_next, ta = ta_next, tb = tb_next;
     if (st + 1 < nsteps) prefetch(st + 1);
     // (a) right-hand side of row r
     if (own) {
       float vr, vi;
       if (fwd) {
-        cd d = fv;
-        if (MODE == 1 && ftr >= 0) d = cadd(d, cscale(cadd(ta, tb), (double)fsg));
-        vr = (float)d.x - (c.x * chain.x - c.y * chain.y);
-        vi = (float)d.y - (c.x * chain.y + c.y * chain.x);
+        float dr = fv.x, di = fv.y;
+        if (MODE == 1 && ftr >= 0) {
+          dr = fmaf(fsg, ta.x + tb.x, dr);
+          di = fmaf(fsg, ta.y + tb.y, di);
+        }
+        vr = dr - (c.x * chain.x - c.y * chain.y);
+        vi = di - (c.x * chain.y + c.y * chain.x);
       } else {
         vr = c.x * chain.x - c.y * chain.y;
         vi = c.x * chain.y + c.y * chain.x;
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
             if (emit >= 0)
               out[(size_t)s * T4n + (size_t)emit * nt + i] = make_double2(-(double)chain.x, -(double)chain.y);
           } else if (in_layer) {
-            out[(size_t)s * g.Nz * nt + frow + i] = make_double2((double)chain.x, (double)chain.y);
+            vol[(size_t)s * g.Nz * nt + frow + i] = chain;
           }
         }
       }
@@ -487,22 +496,48 @@ __global__ void __launch_bounds__(kPropThreads)
   }
 }
 
+// complex64 copies of FP64 data for the column steps, and the FP64 volume from its
+// complex64 result: elementwise, spread over every SM
+__global__ void to_c64_kernel(const cd* __restrict__ a, size_t n, cf* __restrict__ b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const cd v = a[k];
+    b[k] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void to_c128_kernel(const cf* __restrict__ a, size_t n, cd* __restrict__ b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const cf v = a[k];
+    b[k] = make_double2((double)v.x, (double)v.y);
+  }
+}
+cudaError_t launch_to_c64(const cd* a, size_t n, cf* b, cudaStream_t s) {
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+  to_c64_kernel<<<grid, 256, 0, s>>>(a, n, b);
+  return cudaGetLastError();
+}
+
+// f32: complex64 copy of the sources (S x N_z x n_t, made by the caller with launch_to_c64);
+// MODE 1: xtr32 scratch for the trace forcing and vol32 for the volume (S x N_z x n_t)
 cudaError_t launch_layer_solve_chunked(int mode, const Geometry& g, const LayerInfo* layers, int nloc_max, int K,
-                                       const cf* Tm, const cf* Shi, const cf* Whi, const cf* Ehi, const cd* f,
-                                       const cd* xtr, cd* Y, size_t ystride, cd* out, const int* flag, cf* bnd,
-                                       int nsrc, int* status, cudaStream_t s) {
+                                       const cf* Tm, const cf* Shi, const cf* Whi, const cf* Ehi, const cf* f32,
+                                       const cd* xtr, cf* xtr32, cd* Y, size_t ystride, cd* out, cf* vol32,
+                                       const int* flag, cf* bnd, int nsrc, int* status, cudaStream_t s) {
   if (nloc_max < 1 || nloc_max > kMaxNloc || nloc_max * kChunkQ > kChunkThreads || K < 1 || K > 64)
     return cudaErrorInvalidValue;
-  if (nloc_max * 4 > kPropThreads) return cudaErrorInvalidValue;
   cf* Yc = reinterpret_cast<cf*>(Y);
   const size_t smem = chunk_solve_smem(nloc_max);
   const dim3 grid(g.L * K, nsrc);
-  cudaError_t e;
+  const size_t T4n = (size_t)4 * (g.L - 1) * g.nt;
+  cudaError_t e = cudaSuccess;
+  if (mode == 1) {
+    e = launch_to_c64(xtr, (size_t)nsrc * T4n, xtr32, s);
+    if (e != cudaSuccess) return e;
+  }
   auto go = [&](auto kern) {
     cudaError_t err = smem_limit_max(reinterpret_cast<const void*>(kern));
     if (err != cudaSuccess) return err;
-    kern<<<grid, kChunkThreads, smem, s>>>(g, layers, K, Shi, Whi, Ehi, f, xtr, Yc, ystride, out, flag, nloc_max,
-                                           bnd, status);
+    kern<<<grid, kChunkThreads, smem, s>>>(g, layers, K, Shi, Whi, Ehi, f32, xtr32, Yc, ystride, out, vol32, flag,
+                                           nloc_max, bnd, status);
     return cudaGetLastError();
   };
   if (K > 1) {  // with one chunk the boundary values are zero and phase 1 has nothing to give
@@ -515,7 +550,11 @@ cudaError_t launch_layer_solve_chunked(int mode, const Geometry& g, const LayerI
   chunk_propagate_kernel<<<dim3(g.L, nsrc), kPropThreads, psmem, s>>>(g, layers, K, nloc_max, Tm, flag, mode, bnd);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return mode == 0 ? go(layer_solve_chunk_kernel<0, 3>) : go(layer_solve_chunk_kernel<1, 3>);
+  e = mode == 0 ? go(layer_solve_chunk_kernel<0, 3>) : go(layer_solve_chunk_kernel<1, 3>);
+  if (e != cudaSuccess || mode == 0) return e;
+  const size_t nv = (size_t)nsrc * g.Nz * g.nt;
+  to_c128_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(vol32, nv, out);
+  return cudaGetLastError();
 }
 
 }  // namespace pt
