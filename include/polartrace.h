@@ -253,8 +253,14 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * between steps (default; used when the shape fits its register and shared-
  * memory bounds, and never inside pt_solve_many, whose contexts share the
  * GPU); 1 = one launch per step.  Both give the same products.
+ * PT_OPT_RELAX: GMRES matvecs of PT_MIXED_FP32 - 1 = inexact Krylov
+ * relaxation (default): once the residual estimate of every active source
+ * is below 1e4 rel_tol ||b||, the matvec uses the FP32 blocks instead of the
+ * double-float ones (the residual gap this opens stays about 1e-2 rel_tol
+ * ||b||; the restart residual is always double-float); 0 = double-float
+ * matvecs throughout.
  * PT_ERR_ARG for an unknown option or value. */
-enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3, PT_OPT_SWEEP = 4 };
+enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3, PT_OPT_SWEEP = 4, PT_OPT_RELAX = 5 };
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
 
 /* ---- learned preconditioner correction (not in the paper) ------------------
@@ -330,6 +336,10 @@ pt_status pt_last_solve_stats(const pt_ctx* ctx, int64_t* kernel_launches, int32
 /* Restart cycles of the last pt_solve (each ends with an explicit residual) and
  * how many of them applied the learned correction (host outputs, NULL allowed). */
 pt_status pt_last_solve_cycles(const pt_ctx* ctx, int32_t* cycles, int32_t* learned_cycles);
+
+/* Matvecs of the last pt_solve that ran in FP32 under PT_OPT_RELAX.
+ * PT_ERR_ARG for a NULL argument. */
+pt_status pt_last_solve_relaxed(const pt_ctx* ctx, int32_t* relaxed_matvecs);
 
 void pt_destroy(pt_ctx* ctx);
 const char* pt_status_string(pt_status s);

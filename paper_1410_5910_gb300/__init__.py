@@ -16,9 +16,9 @@ import math
 
 import torch
 
-from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, PT_OPT_LEARNED, PT_OPT_LOCAL_SOLVE, PT_OPT_SWEEP, Params, PolarTraceError, check, lib
+from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, PT_OPT_LEARNED, PT_OPT_LOCAL_SOLVE, PT_OPT_RELAX, PT_OPT_SWEEP, Params, PolarTraceError, check, lib
 
-__all__ = ["PolarTrace", "PolarTraceError", "solve_many", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "PT_OPT_LOCAL_SOLVE", "PT_OPT_SWEEP", "default_pml_strength",
+__all__ = ["PolarTrace", "PolarTraceError", "solve_many", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "PT_OPT_LOCAL_SOLVE", "PT_OPT_RELAX", "PT_OPT_SWEEP", "default_pml_strength",
            "layer_partition"]
 
 
@@ -182,6 +182,12 @@ class PolarTrace:
         a, b = C.c_int32(), C.c_int32()
         check(lib().pt_last_solve_cycles(self._ctx, C.byref(a), C.byref(b)), "pt_last_solve_cycles")
         return a.value, b.value
+
+    def last_solve_relaxed(self) -> int:
+        """Matvecs of the last solve that ran in FP32 under PT_OPT_RELAX."""
+        a = C.c_int32()
+        check(lib().pt_last_solve_relaxed(self._ctx, C.byref(a)), "pt_last_solve_relaxed")
+        return a.value
 
     # ---- building blocks (testing) -----------------------------------------
     def _vec(self, S):

@@ -24,12 +24,13 @@ EXPORTS = [
     "pt_destroy", "pt_status_string", "pt_last_error", "pt_rhs_noalloc", "pt_apply", "pt_plr_stats",
     "pt_volume_residual", "pt_set_option", "pt_correction_nparams", "pt_set_correction", "pt_get_correction",
     "pt_correction_scratch_bytes", "pt_correction_forward", "pt_correction_grad", "pt_train_bytes",
-    "pt_train_correction", "pt_apply_correction", "pt_last_solve_cycles", "pt_solve_many",
+    "pt_train_correction", "pt_apply_correction", "pt_last_solve_cycles", "pt_solve_many", "pt_last_solve_relaxed",
 ]
 PT_OPT_LAYER_GROUP = 1
 PT_OPT_LEARNED = 2
 PT_OPT_LOCAL_SOLVE = 3
 PT_OPT_SWEEP = 4
+PT_OPT_RELAX = 5
 
 
 class Params(C.Structure):
@@ -88,6 +89,7 @@ def lib() -> C.CDLL:
     L.pt_apply_correction.argtypes = [vp, i32, vp, vp, vp, sz]
     L.pt_last_solve_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
     L.pt_last_solve_cycles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.pt_last_solve_relaxed.argtypes = [vp, C.POINTER(i32)]
     L.pt_solve_many.argtypes = [i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(vp), C.POINTER(vp), f64, i32,
                                 C.POINTER(vp), C.POINTER(sz), C.POINTER(i32), C.POINTER(f64), C.POINTER(i32)]
     L.pt_destroy.argtypes = [vp]

@@ -207,6 +207,30 @@ def test_chunked_local_solves_match_oracle_medium(sources):
         assert _rel(u4[q].cpu().numpy(), u0[q].cpu().numpy()) < 1e-5
 
 
+@pytest.mark.parametrize("tol", [1e-7, 1e-10])
+def test_relaxed_matvecs_keep_the_tolerance(tol):
+    """Inexact Krylov relaxation of the mixed form (FP32 matvecs once the residual estimate is below 1e4 tol ||b||)
+    against double-float matvecs throughout: both reach tol (the restart residual is double-float), the same
+    iteration count up to one, some matvecs relaxed, the fields within the FP32 local-solve accuracy of each other
+    and of the oracle."""
+    from paper_1410_5910_gb300 import PT_OPT_RELAX
+
+    wl = W.small_case(200, 120, 10, 4, medium="grf", seed=7, sources=((100, 60), (30, 100)))
+    prob, solver = _mk(wl, precision=1, max_sources=2)
+    ft = torch.from_numpy(wl.f()).cuda()
+    u1, _, its1, rel1 = solver.solve(ft, tol=tol)
+    n_relaxed = solver.last_solve_relaxed()
+    solver.set_option(PT_OPT_RELAX, 0)
+    u0, _, its0, rel0 = solver.solve(ft, tol=tol)
+    assert solver.last_solve_relaxed() == 0 and n_relaxed >= 1
+    ref = S.global_solve(prob, wl.f())
+    for q in range(2):
+        assert rel1[q] <= tol and rel0[q] <= tol
+        assert abs(its1[q] - its0[q]) <= 1
+        assert _rel(u1[q].cpu().numpy(), u0[q].cpu().numpy()) < 1e-5
+        assert _rel(u1[q].cpu().numpy(), ref[q]) < max(1e-5, 10 * tol)
+
+
 def test_batched_sources_equal_single_solves():
     wl = W.small_case(40, 60, 8, 3, medium="grf", seed=11)
     prob, solver = _mk(wl, max_sources=3)
