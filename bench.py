@@ -265,11 +265,12 @@ def batched_section(args, dev, pg, pk):
 
 def uneven_section(args, dev, pg):
     """Uneven batch: independent problems of the GRF family with different sizes, layer counts and source
-    counts (mixed form), solved one instance after another and concurrently (pt_solve_many, one stream per
-    instance).  Offline phases excluded."""
+    counts (mixed form with FP16 preconditioner blocks: the concurrent instances take the per-step sweeps,
+    whose bytes the FP16 copies halve), solved one instance after another and concurrently (pt_solve_many,
+    one stream per instance).  Offline phases excluded."""
     import torch
 
-    from paper_1410_5910_gb300 import PT_MIXED_FP32, PolarTrace, default_pml_strength, solve_many
+    from paper_1410_5910_gb300 import PT_MIXED_FP32, PT_OPT_PRECOND_FP16, PolarTrace, default_pml_strength, solve_many
 
     cases = W.uneven_batch(count=args.uneven_count, nmin=255, nmax=args.uneven_nmax, Lmin=8, Lmax=16)
     solvers, fs = [], []
@@ -280,6 +281,7 @@ def uneven_section(args, dev, pg):
         sv = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, om, torch.from_numpy(c).to(dev),
                         pml_C=default_pml_strength(float(c.max())), precision=PT_MIXED_FP32,
                         max_sources=len(wl.sources), max_krylov=40, stream=torch.cuda.Stream(dev))
+        sv.set_option(PT_OPT_PRECOND_FP16, 1)
         solvers.append(sv)
         fs.append(torch.from_numpy(wl.f()).to(dev))
     torch.cuda.synchronize(dev)
@@ -297,7 +299,7 @@ def uneven_section(args, dev, pg):
     out = {"instances": len(cases), "sources": nsol, "offline_s": t_off,
            "n_range": [min(w.nx for w in cases), max(w.nx for w in cases)],
            "L_range": [min(w.L for w in cases), max(w.L for w in cases)],
-           "form": "mixed, one stream and one host thread per instance"}
+           "form": "mixed with FP16 preconditioner blocks, one stream and one host thread per instance"}
     for name, fn in (("sequential", sequential), ("concurrent", concurrent)):
         fn()
         barrier(pg)

@@ -64,8 +64,9 @@ typedef enum {
 typedef enum {
   PT_FP64 = 0,       /* every block product in FP64                                  */
   PT_MIXED_FP32 = 1, /* preconditioner (Algorithm 4) applies FP32 copies of the
-                        blocks; the GMRES matvec runs in double-float (FP32 pairs,
-                        ~1e-14); local solves (right-hand side, reconstruction) in
+                        blocks (FP16 ones by option); the GMRES
+                        matvec runs in double-float (FP32 pairs, ~1e-14); local
+                        solves (right-hand side, reconstruction) in
                         FP32 with the FP64 factors rounded to complex64, chunked
                         along x (~1e-6 on the field; PT_OPT_LOCAL_SOLVE = 1
                         selects double-float);
@@ -259,8 +260,21 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * double-float ones (the residual gap this opens stays about 1e-2 rel_tol
  * ||b||; the restart residual is always double-float); 0 = double-float
  * matvecs throughout.
+ * PT_OPT_PRECOND_FP16: block products of the PT_MIXED_FP32 preconditioner
+ * (Algorithm 4: the sweeps D^{-1} and R) - 0 = the complex64 copies (default,
+ * about 1e-7); 1 = FP16 copies of the blocks, each block row scaled by a
+ * power of two into FP16 range (plr = 0 only; about 5e-4 relative on the
+ * preconditioner's output: half the bytes of every sweep step and R apply,
+ * sometimes one more GMRES iteration).
  * PT_ERR_ARG for an unknown option or value. */
-enum { PT_OPT_LAYER_GROUP = 1, PT_OPT_LEARNED = 2, PT_OPT_LOCAL_SOLVE = 3, PT_OPT_SWEEP = 4, PT_OPT_RELAX = 5 };
+enum {
+  PT_OPT_LAYER_GROUP = 1,
+  PT_OPT_LEARNED = 2,
+  PT_OPT_LOCAL_SOLVE = 3,
+  PT_OPT_SWEEP = 4,
+  PT_OPT_RELAX = 5,
+  PT_OPT_PRECOND_FP16 = 6
+};
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
 
 /* ---- learned preconditioner correction (not in the paper) ------------------

@@ -91,10 +91,11 @@ cudaError_t launch_layer_solve_chunked(int, const Geometry&, const LayerInfo*, i
                                        const cf*, const cf*, const cf*, const cd*, cf*, cd*, size_t, cd*, cf*,
                                        const int*, cf*, int, int*, cudaStream_t);
 cudaError_t launch_prep_inputs(const cd*, int, int, int, bool, void*, cudaStream_t);
-cudaError_t launch_apply_lowp(int, int, int, int, const ApplyRow*, int, const cf*, const cf*, const void*, const cd*,
-                              const cd*, cd*, int, int, double, double, cudaStream_t);
-bool launch_sweep_f32(int, int, int, int, const ApplyRow*, const void*, const cd*, cd*, cf*, int, unsigned*, int*,
-                      cudaStream_t, cudaError_t*);
+cudaError_t launch_apply_lowp(int, int, int, int, const ApplyRow*, int, const void*, const void*, const void*,
+                              const cd*, const cd*, cd*, int, int, double, double, cudaStream_t);
+cudaError_t launch_blocks_h16(const cd*, int, int, size_t, __half2*, float*, cudaStream_t);
+bool launch_sweep_f32(int, int, int, int, const ApplyRow*, const void*, const float*, const cd*, cd*, cf*, int,
+                      unsigned*, int*, cudaStream_t, cudaError_t*);
 cudaError_t launch_volume_residual(const Geometry&, const double*, const cd*, const cd*, int, double*, cudaStream_t);
 cudaError_t launch_dots(const cd*, int, size_t, const cd*, int, cd*, cd*, int, cd*, int, int, int, cudaStream_t);
 cudaError_t launch_update(const cd*, int, size_t, cd*, int, const cd*, int, cudaStream_t);
@@ -284,6 +285,8 @@ struct Persist {
   cf* sweep_y32;        // complex64 copies of the traces a one-launch sweep writes (mixed FP32 form)
   void* xprep;          // inputs of the FP32 / double-float applies converted once per application
   cf* chunk_T;          // Phi_k, M_k, Psi_k of the chunked local solves: [kr set | kv set][L][K][3][nloc_max^2]
+  __half2* blocks_h16;  // mixed FP32 form: FP16 block copies for the preconditioner, rows padded to ld32
+  float* bscale;        // and one scale per block row
   cd* W;
   cd* E;
   cd* Sinv;
@@ -353,7 +356,11 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
     q.e_hi = c.take<cf>(P.coef_elems);
     q.e_lo = c.take<cf>(P.coef_elems);
   }
-  if (p->precision == PT_MIXED_FP32 && !P.plr) q.sweep_y32 = c.take<cf>((size_t)p->max_sources * P.T4 * P.nt);
+  if (p->precision == PT_MIXED_FP32 && !P.plr) {
+    q.sweep_y32 = c.take<cf>((size_t)p->max_sources * P.T4 * P.nt);
+    q.blocks_h16 = c.take<__half2>((size_t)P.L * 16 * P.nt * P.ld32);
+    q.bscale = c.take<float>((size_t)P.L * 16 * P.nt);
+  }
   if (p->precision != PT_FP64 && !P.plr) q.xprep = c.take<float4>((size_t)p->max_sources * P.T4 * P.ld32);
   if (P.kr > 0)
     q.chunk_T = c.take<cf>((size_t)P.L * (P.kr + P.kv) * 3 * P.nloc_max * P.nloc_max);
@@ -704,6 +711,7 @@ struct pt_ctx {
   int opt_local_solve = 0;  // PT_OPT_LOCAL_SOLVE
   int opt_sweep = 0;        // PT_OPT_SWEEP
   int opt_relax = 0;        // PT_OPT_RELAX
+  int opt_precond16 = 0;    // PT_OPT_PRECOND_FP16
   int relaxed_matvecs = 0;  // FP32 matvecs of the last solve
   bool sweep_fusable = false;  // sweep tables have the pair layout of the one-launch sweep
   // learned correction
@@ -903,6 +911,8 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   c->d = carve_persist(P, prm, persistent, nullptr);
   if (c->d.chunk_T) c->opt_local_solve = 4;  // mixed FP32: chunked local solves by default
   if (prm->precision == PT_MIXED_FP32) c->opt_relax = 1;
+  // FP16 preconditioner blocks are an option: on the 511 x 1023, L = 16 workload they cost one
+  // more GMRES iteration than the complex64 ones, which outweighs the halved sweep stream
   auto bail = [&](pt_status s) { delete c; return s; };
   cudaStream_t s = c->stream;
   const Geometry& g = P.g;
@@ -937,6 +947,8 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
                        c->d.E, static_cast<cd*>(setup), setup_slot_elems(P), c->d.blocks, s);
   if (e == cudaSuccess && c->d.blocks_hi)
     e = launch_split_blocks(c->d.blocks, P.nt, P.ld32, (size_t)P.L * 16 * P.nt, c->d.blocks_hi, c->d.blocks_lo, s);
+  if (e == cudaSuccess && c->d.blocks_h16)
+    e = launch_blocks_h16(c->d.blocks, P.nt, P.ld32, (size_t)P.L * 16 * P.nt, c->d.blocks_h16, c->d.bscale, s);
   if (e == cudaSuccess && c->d.sinv_hi) e = launch_split_sinv(c->d.Sinv, P.sinv_elems, c->d.sinv_hi, c->d.sinv_lo, s);
   if (e == cudaSuccess && c->d.w_hi) e = launch_split_sinv(c->d.W, P.coef_elems, c->d.w_hi, c->d.w_lo, s);
   if (e == cudaSuccess && c->d.e_hi) e = launch_split_sinv(c->d.E, P.coef_elems, c->d.e_hi, c->d.e_lo, s);
@@ -991,7 +1003,7 @@ static pt_status bind_call(pt_ctx* c, const SolveBufs& B, int S) {
 // ---- online building blocks ------------------------------------------------
 namespace {
 
-enum { kModeFP64 = 0, kModeFP32 = 1, kModeDF = 2, kModeTC1 = 3, kModeTC3 = 4 };
+enum { kModeFP64 = 0, kModeFP32 = 1, kModeDF = 2, kModeTC1 = 3, kModeTC3 = 4, kModeH16 = 5 };
 
 bool mixed(const pt_ctx* c) { return c->prm.precision == PT_MIXED_FP32 || c->prm.precision == PT_MIXED_TC; }
 bool tcmode(const pt_ctx* c) { return c->prm.precision == PT_MIXED_TC; }
@@ -1042,14 +1054,18 @@ cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, cons
                               c->stream, &e))
       return e;
   }
-  if ((mode == kModeFP32 || mode == kModeDF) && c->d.xprep && !P.plr) {
+  if ((mode == kModeFP32 || mode == kModeDF || (mode == kModeH16 && c->d.blocks_h16)) && c->d.xprep && !P.plr) {
     // inputs converted once, FP32 staging, FP64 epilogue on one thread per row
     c->launches++;
     cudaError_t e = launch_prep_inputs(x, S * P.T4, P.nt, P.ld32, mode == kModeDF, c->d.xprep, c->stream);
     if (e != cudaSuccess) return e;
+    if (mode == kModeH16)  // FP16 blocks with row scales (kernel mode 3)
+      return launch_apply_lowp(3, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_h16, c->d.bscale, c->d.xprep, x,
+                               aux, y, S, rows_per_cta, alpha, beta, c->stream);
     return launch_apply_lowp(mode, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, c->d.blocks_lo,
                              c->d.xprep, x, aux, y, S, rows_per_cta, alpha, beta, c->stream);
   }
+  if (mode == kModeH16) mode = kModeFP32;  // no FP16 copies: the FP32 ones
   return launch_apply_mode(mode, P.nt, P.ld32, P.T4, op.table, op.nrows, c->d.blocks_hi, c->d.blocks_lo, x, aux, y,
                            S, rows_per_cta, alpha, beta, c->stream);
 }
@@ -1115,12 +1131,16 @@ cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working
     cudaError_t e = tc_scale(c, S, r);
     if (e != cudaSuccess) return e;
   }
-  if (mode == kModeFP32 && !c->P.plr && c->sweep_fusable && c->opt_sweep == 0 && !g_shared_gpu) {
+  if ((mode == kModeFP32 || mode == kModeH16) && !c->P.plr && c->sweep_fusable && c->opt_sweep == 0 &&
+      !g_shared_gpu) {
     // all steps in one cooperative launch (the counter reset is the second operation)
     cudaError_t e = cudaSuccess;
+    const bool h16 = mode == kModeH16 && c->d.blocks_h16;
     if (c->d.sweep_y32 &&
-        launch_sweep_f32(c->P.nt, c->P.ld32, c->P.T4, steps, c->d.tab_sweep, c->d.blocks_hi, r, y, c->d.sweep_y32, S,
-                         c->d.sweep_bar, c->d.status, c->stream, &e)) {
+        launch_sweep_f32(c->P.nt, c->P.ld32, c->P.T4, steps, c->d.tab_sweep,
+                         h16 ? static_cast<const void*>(c->d.blocks_h16) : static_cast<const void*>(c->d.blocks_hi),
+                         h16 ? c->d.bscale : nullptr, r, y, c->d.sweep_y32, S, c->d.sweep_bar, c->d.status,
+                         c->stream, &e)) {
       c->launches += 2;
       return e;
     }
@@ -1134,8 +1154,16 @@ cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working
 
 // Algorithm 4: z = D^{-1} r; repeat n_it - 1 times z = D^{-1}(r - R z).
 // Mixed form: FP32 blocks (the preconditioner only has to be approximate in flexible GMRES).
+// the arithmetic of the preconditioner's products: FP16 blocks (mixed FP32 form, by default),
+// FP32 blocks, the tensor cores, or FP64
+int precond_mode(const pt_ctx* c) {
+  if (tcmode(c)) return kModeTC1;
+  if (!mixed(c)) return kModeFP64;
+  return (c->opt_precond16 && c->d.blocks_h16) ? kModeH16 : kModeFP32;
+}
+
 cudaError_t do_precond(pt_ctx* c, int S, const cd* r, cd* z, cd* tmp1, cd* /*tmp2*/) {
-  const int mode = tcmode(c) ? kModeTC1 : (mixed(c) ? kModeFP32 : kModeFP64);
+  const int mode = precond_mode(c);
   cudaError_t e = do_Dinv(c, S, r, z, mode, true);
   for (int it = 1; it < c->prm.gs_iters && e == cudaSuccess; ++it) {
     e = do_R(c, S, z, tmp1, mode, -1.0, 1.0, r, true);  // tmp1 = r - R z
@@ -1218,7 +1246,7 @@ extern "C" pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32
   if (which == 0) {
     PT_CUDA(do_matvec(ctx, nsrc, xd, yd, !w));
   } else {
-    const int mode = (w && tcmode(ctx)) ? kModeTC1 : ((w && mixed(ctx)) ? kModeFP32 : kModeFP64);
+    const int mode = w ? precond_mode(ctx) : kModeFP64;
     if (which == 1) PT_CUDA(do_R(ctx, nsrc, xd, yd, mode, 1.0, 0.0, nullptr, w));
     else PT_CUDA(do_Dinv(ctx, nsrc, xd, yd, mode, w));
   }
@@ -1254,6 +1282,12 @@ extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
     if (value < 0 || value > 4) return fail(PT_ERR_ARG, "PT_OPT_LOCAL_SOLVE must be 0, 1, 2, 3 or 4");
     if (value == 4 && !ctx->d.chunk_T) return fail(PT_ERR_ARG, "chunked local solves need PT_MIXED_FP32");
     ctx->opt_local_solve = value;
+    return PT_OK;
+  }
+  if (option == PT_OPT_PRECOND_FP16) {
+    if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_PRECOND_FP16 must be 0 or 1");
+    if (value == 1 && !ctx->d.blocks_h16) return fail(PT_ERR_ARG, "FP16 preconditioner blocks need PT_MIXED_FP32, plr = 0");
+    ctx->opt_precond16 = value;
     return PT_OK;
   }
   if (option == PT_OPT_RELAX) {

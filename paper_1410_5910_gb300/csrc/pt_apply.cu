@@ -20,11 +20,14 @@
 // sources fastest so that a batch of sources shares each block row through L2.
 #include "pt_common.cuh"
 
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <type_traits>
 
 namespace pt {
 
-enum ApplyMode { kFP64 = 0, kFP32 = 1, kDF = 2 };
+enum ApplyMode { kFP64 = 0, kFP32 = 1, kDF = 2, kH16 = 3 };
 
 // s + e = a + b exactly (Knuth's two-sum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -273,8 +276,8 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
 
 template <int MODE>
 __global__ void __launch_bounds__(256) apply_lowp_kernel(int nt, int ld, int T4, const ApplyRow* __restrict__ table,
-                                                         const cf* __restrict__ blocks_a,
-                                                         const cf* __restrict__ blocks_b,
+                                                         const void* __restrict__ blocks_a,
+                                                         const void* __restrict__ blocks_b,
                                                          const void* __restrict__ xp, const cd* x,
                                                          const cd* __restrict__ aux, cd* y, int rows_per_cta,
                                                          double alpha, double beta) {
@@ -328,11 +331,42 @@ __global__ void __launch_bounds__(256) apply_lowp_kernel(int nt, int ld, int T4,
   for (int rr = warp; rr < rows_per_cta; rr += 8) {
     const int r = r0 + rr;
     if (r >= nt) break;
-    if (MODE == kFP32) {
+    if (MODE == kH16) {
+      // FP16 block rows, one power-of-two scale per block row: partial sums per term, scaled
       const float4* xin = reinterpret_cast<const float4*>(smem_raw);  // two complex64 per float4
       float are = 0.f, aim = 0.f;
       for (int t = 0; t < nterms; ++t) {
-        const float4* B = reinterpret_cast<const float4*>(blocks_a + (size_t)row.t[t].block * bsz + (size_t)r * ld);
+        const int blk = row.t[t].block;
+        const uint2* B = reinterpret_cast<const uint2*>(static_cast<const __half2*>(blocks_a) + (size_t)blk * bsz +
+                                                        (size_t)r * ld);
+        const float sc = __ldg(static_cast<const float*>(blocks_b) + (size_t)blk * nt + r);
+        const float4* xv = xin + t * np;
+        float tre = 0.f, tim = 0.f;
+        for (int k = lane; k < np; k += 32) {
+          const uint2 hb = __ldg(B + k);
+          const float4 v = xv[k];
+          const float2 b0 = __half22float2(*reinterpret_cast<const __half2*>(&hb.x));
+          const float2 b1 = __half22float2(*reinterpret_cast<const __half2*>(&hb.y));
+          tre = fmaf(b0.x, v.x, tre);
+          tre = fmaf(-b0.y, v.y, tre);
+          tre = fmaf(b1.x, v.z, tre);
+          tre = fmaf(-b1.y, v.w, tre);
+          tim = fmaf(b0.x, v.y, tim);
+          tim = fmaf(b0.y, v.x, tim);
+          tim = fmaf(b1.x, v.w, tim);
+          tim = fmaf(b1.y, v.z, tim);
+        }
+        are = fmaf(tre, sc, are);
+        aim = fmaf(tim, sc, aim);
+      }
+      const cf acc = warp_sum_cf(make_float2(are, aim));
+      if (lane == 0) res[rr] = make_float4(acc.x, acc.y, 0.f, 0.f);
+    } else if (MODE == kFP32) {
+      const float4* xin = reinterpret_cast<const float4*>(smem_raw);  // two complex64 per float4
+      float are = 0.f, aim = 0.f;
+      for (int t = 0; t < nterms; ++t) {
+        const float4* B = reinterpret_cast<const float4*>(static_cast<const cf*>(blocks_a) +
+                                                          (size_t)row.t[t].block * bsz + (size_t)r * ld);
         const float4* xv = xin + t * np;
         int k = lane;
         for (; k + 96 < np; k += 128) {
@@ -372,8 +406,8 @@ __global__ void __launch_bounds__(256) apply_lowp_kernel(int nt, int ld, int T4,
       float Sr2 = 0.f, Cr2 = 0.f, Si2 = 0.f, Ci2 = 0.f;
       for (int t = 0; t < nterms; ++t) {
         const size_t off = (size_t)row.t[t].block * bsz + (size_t)r * ld;
-        const float4* H = reinterpret_cast<const float4*>(blocks_a + off);
-        const float4* Lo = reinterpret_cast<const float4*>(blocks_b + off);
+        const float4* H = reinterpret_cast<const float4*>(static_cast<const cf*>(blocks_a) + off);
+        const float4* Lo = reinterpret_cast<const float4*>(static_cast<const cf*>(blocks_b) + off);
         const float4* xv = xin + t * ld;
         int k = lane;
         // the next pair of columns' block values is loaded while the current pair computes
@@ -461,25 +495,57 @@ __global__ void __launch_bounds__(256) apply_lowp_kernel(int nt, int ld, int T4,
   }
 }
 
-cudaError_t launch_apply_lowp(int mode, int nt, int ld, int T4, const ApplyRow* table, int nrows, const cf* blocks_a,
-                              const cf* blocks_b, const void* xp, const cd* x, const cd* aux, cd* y, int nsrc,
+// mode kFP32 (blocks_a: complex64 blocks), kDF (blocks_a / blocks_b: hi / lo complex64) or
+// kH16 (blocks_a: FP16 (re, im) pairs, blocks_b: one float scale per block row)
+cudaError_t launch_apply_lowp(int mode, int nt, int ld, int T4, const ApplyRow* table, int nrows, const void* blocks_a,
+                              const void* blocks_b, const void* xp, const cd* x, const cd* aux, cd* y, int nsrc,
                               int rows_per_cta, double alpha, double beta, cudaStream_t s) {
   if (rows_per_cta > 256) return cudaErrorInvalidValue;
   const int elem = mode == kDF ? 16 : 8;
   const size_t smem = 4ull * ld * elem + (size_t)rows_per_cta * sizeof(float4);
   dim3 grid(nsrc, (nt + rows_per_cta - 1) / rows_per_cta, nrows);
-  cudaError_t e;
-  if (mode == kDF) {
-    e = smem_limit_max(reinterpret_cast<const void*>(apply_lowp_kernel<kDF>));
+  auto go = [&](auto kern) {
+    cudaError_t e = smem_limit_max(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
-    apply_lowp_kernel<kDF><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, xp, x, aux, y,
-                                                   rows_per_cta, alpha, beta);
-  } else {
-    e = smem_limit_max(reinterpret_cast<const void*>(apply_lowp_kernel<kFP32>));
-    if (e != cudaSuccess) return e;
-    apply_lowp_kernel<kFP32><<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, xp, x, aux, y,
-                                                     rows_per_cta, alpha, beta);
+    kern<<<grid, 256, smem, s>>>(nt, ld, T4, table, blocks_a, blocks_b, xp, x, aux, y, rows_per_cta, alpha, beta);
+    return cudaGetLastError();
+  };
+  if (mode == kDF) return go(apply_lowp_kernel<kDF>);
+  if (mode == kH16) return go(apply_lowp_kernel<kH16>);
+  return go(apply_lowp_kernel<kFP32>);
+}
+
+// FP16 copies of the blocks for the mixed preconditioner: one warp per block row takes the
+// row's largest |Re|, |Im| (FP64), picks the power of two 2^p that brings it into
+// [2^13, 2^14), stores fl16(2^p b) as (re, im) pairs (rows padded to ld with zeros) and the
+// row's scale 2^-p; an entry keeps 11 significant bits unless it is 2^-27 of the row's largest
+__global__ void blocks_h16_kernel(const cd* __restrict__ src, int nt, int ld, size_t nrows_total,
+                                  __half2* __restrict__ out, float* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const size_t w0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+  const size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t q = w0; q < nrows_total; q += nw) {
+    const cd* row = src + q * nt;
+    double m = 0.0;
+    for (int k = lane; k < nt; k += 32) m = fmax(m, fmax(fabs(row[k].x), fabs(row[k].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);  // m in [2^(ex-1), 2^ex)
+    const int p = m > 0.0 ? 14 - ex : 0;
+    const double mult = ldexp(1.0, p);
+    for (int k = lane; k < ld; k += 32) {
+      float2 v = make_float2(0.f, 0.f);
+      if (k < nt) v = make_float2((float)(row[k].x * mult), (float)(row[k].y * mult));
+      out[q * ld + k] = __floats2half2_rn(v.x, v.y);
+    }
+    if (lane == 0) scale[q] = (float)ldexp(1.0, -p);
   }
+}
+
+cudaError_t launch_blocks_h16(const cd* src, int nt, int ld, size_t nrows_total, __half2* out, float* scale,
+                              cudaStream_t s) {
+  blocks_h16_kernel<<<1216, 256, 0, s>>>(src, nt, ld, nrows_total, out, scale);
   return cudaGetLastError();
 }
 
@@ -646,18 +712,21 @@ __device__ __forceinline__ bool sweep_mb_wait(uint64_t* mb, int parity, int* sta
   return false;
 }
 
-template <int MAXC>
+// H16: FP16 block rows ((re, im) pairs) with one float scale per block row (bscale), half
+// the bytes per step; products per term in FP32, scaled, then summed
+template <int MAXC, bool H16>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_f32_kernel(int nt, int ld, int T4, int nsteps, const ApplyRow* __restrict__ table,
-                     const cf* __restrict__ blocks, const cd* __restrict__ aux, cd* y, cf* y32, int S,
-                     unsigned* bar, int* status) {
+                     const void* __restrict__ blocks, const float* __restrict__ bscale, const cd* __restrict__ aux,
+                     cd* y, cf* y32, int S, unsigned* bar, int* status) {
+  using E = typename std::conditional<H16, __half2, cf>::type;  // one complex block entry
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int abort_flag;
   // [step table: 4 nsteps rows][block rows: warp x term x ld][inputs: S x (2 g + t) x ld]
   // [row sums: warp x S][one mbarrier per warp]
   ApplyRow* tab = reinterpret_cast<ApplyRow*>(smem_raw);
-  cf* buf = reinterpret_cast<cf*>(smem_raw + (size_t)4 * nsteps * sizeof(ApplyRow));
-  cf* xin = buf + (size_t)kSweepWarps * 2 * ld;
+  E* buf = reinterpret_cast<E*>(smem_raw + (size_t)4 * nsteps * sizeof(ApplyRow));
+  cf* xin = reinterpret_cast<cf*>(buf + (size_t)kSweepWarps * 2 * ld);
   cf* sums = xin + (size_t)S * 4 * ld;
   uint64_t* mbs = reinterpret_cast<uint64_t*>(sums + (((size_t)kSweepWarps * S + 1) & ~(size_t)1));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -697,11 +766,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   // (one arrival per phase, with the bytes it asked for), so that each warp starts its
   // products as soon as its rows have landed; output threads: their identity terms
   double2 a[2];
+  float sc_next[2] = {1.f, 1.f};  // H16: the row scales of the warp's next block rows
   auto issue = [&](int st) {
+    const ApplyRow* row = tab + 4 * st + qt;
     if (lane == 0) {
-      const ApplyRow* row = tab + 4 * st + qt;
       const int nterms = own ? row->nterms : 0;
-      const uint32_t bytes = (uint32_t)(nterms * ld * sizeof(cf));
+      const uint32_t bytes = (uint32_t)(nterms * ld * sizeof(E));
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of the buffer first
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sweep_saddr(mb)), "r"(bytes)
                    : "memory");
@@ -709,9 +779,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 sweep_saddr(buf + (size_t)(warp * 2 + t) * ld)),
-            "l"(blocks + ((size_t)row->t[t].block * nt + r) * ld), "r"((uint32_t)(ld * sizeof(cf))),
-            "r"(sweep_saddr(mb))
+            "l"(static_cast<const E*>(blocks) + ((size_t)row->t[t].block * nt + r) * ld),
+            "r"((uint32_t)(ld * sizeof(E))), "r"(sweep_saddr(mb))
             : "memory");
+    }
+    if (H16) {
+      const int nterms = own ? row->nterms : 0;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) sc_next[t] = t < nterms ? __ldg(bscale + (size_t)row->t[t].block * nt + r) : 0.f;
     }
     const ApplyRow* orw = tab + 4 * st + oqt;
     const int nid = orw->nid;
@@ -784,6 +859,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     // (2) this warp's block rows landed, (3) its row products (FP32), one sum per source
     //     into shared memory
     const bool ok = sweep_mb_wait(mb, s & 1, status);
+    const float sc0 = sc_next[0], sc1 = sc_next[1];
     if (own && ok) {
       const int nterms = rows[qt].nterms;
       for (int q = 0; q < S; ++q) {
@@ -791,8 +867,32 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         const float4* xv4 = reinterpret_cast<const float4*>(xin + (size_t)q * 4 * ld);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-          if (t < nterms) {
-            const float4* bv4 = reinterpret_cast<const float4*>(buf + (size_t)(warp * 2 + t) * ld);
+          if (H16 && t < nterms) {
+            const uint2* bh = reinterpret_cast<const uint2*>(buf + (size_t)(warp * 2 + t) * ld);
+            float tre = 0.f, tim = 0.f;
+#pragma unroll
+            for (int c = 0; c < MAXC; ++c) {
+              const int k = lane + 32 * c;
+              if (k < np) {
+                const float4 v = xv4[(2 * g + t) * np + k];
+                const uint2 hb = bh[k];
+                const float2 b0 = __half22float2(*reinterpret_cast<const __half2*>(&hb.x));
+                const float2 b1 = __half22float2(*reinterpret_cast<const __half2*>(&hb.y));
+                tre = fmaf(b0.x, v.x, tre);
+                tre = fmaf(-b0.y, v.y, tre);
+                tre = fmaf(b1.x, v.z, tre);
+                tre = fmaf(-b1.y, v.w, tre);
+                tim = fmaf(b0.x, v.y, tim);
+                tim = fmaf(b0.y, v.x, tim);
+                tim = fmaf(b1.x, v.w, tim);
+                tim = fmaf(b1.y, v.z, tim);
+              }
+            }
+            const float sct = t == 0 ? sc0 : sc1;
+            are = fmaf(tre, sct, are);
+            aim = fmaf(tim, sct, aim);
+          } else if (!H16 && t < nterms) {
+            const float4* bv4 = reinterpret_cast<const float4*>(reinterpret_cast<const cf*>(buf) + (size_t)(warp * 2 + t) * ld);
 #pragma unroll
             for (int c = 0; c < MAXC; ++c) {
               const int k = lane + 32 * c;
@@ -839,24 +939,29 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   }
 }
 
-size_t sweep_f32_smem(int ld, int S, int nsteps) {
-  return (size_t)4 * nsteps * sizeof(ApplyRow) + (size_t)kSweepWarps * 2 * ld * sizeof(cf) +
+size_t sweep_f32_smem(int ld, int S, int nsteps, bool h16) {
+  return (size_t)4 * nsteps * sizeof(ApplyRow) + (size_t)kSweepWarps * 2 * ld * (h16 ? sizeof(__half2) : sizeof(cf)) +
          (size_t)S * 4 * ld * sizeof(cf) + ((((size_t)kSweepWarps * S + 1) & ~(size_t)1) * sizeof(cf)) +
          kSweepWarps * sizeof(uint64_t);
 }
 
-// D^{-1} of the FP32 preconditioner in one cooperative launch; y32 (S x T4 x n_t complex64)
-// is scratch.  False (nothing launched) when the shape is outside the kernel's bounds
-// (register tile, shared memory, one warp per row of a step on a co-resident grid).
-bool launch_sweep_f32(int nt, int ld, int T4, int nsteps, const ApplyRow* table, const void* blocks, const cd* aux,
-                      cd* y, cf* y32, int S, unsigned* bar, int* status, cudaStream_t s, cudaError_t* err) {
+// D^{-1} of the mixed preconditioner in one cooperative launch, with complex64 blocks or, when
+// bscale is given, FP16 blocks and their row scales; y32 (S x T4 x n_t complex64) is scratch.
+// False (nothing launched) when the shape is outside the kernel's bounds (register tile,
+// shared memory, one warp per row of a step on a co-resident grid).
+bool launch_sweep_f32(int nt, int ld, int T4, int nsteps, const ApplyRow* table, const void* blocks,
+                      const float* bscale, const cd* aux, cd* y, cf* y32, int S, unsigned* bar, int* status,
+                      cudaStream_t s, cudaError_t* err) {
   const int np = ld >> 1;
+  const bool h16 = bscale != nullptr;
   if (nsteps < 1 || nsteps > 64 || S < 1 || S > 32 || ld > 2 * kSweepThreads) return false;
   const void* fn;
-  if (np <= 32 * 4) fn = reinterpret_cast<const void*>(sweep_f32_kernel<4>);
-  else if (np <= 32 * 9) fn = reinterpret_cast<const void*>(sweep_f32_kernel<9>);
+  if (np <= 32 * 4) fn = h16 ? reinterpret_cast<const void*>(sweep_f32_kernel<4, true>)
+                             : reinterpret_cast<const void*>(sweep_f32_kernel<4, false>);
+  else if (np <= 32 * 9) fn = h16 ? reinterpret_cast<const void*>(sweep_f32_kernel<9, true>)
+                                  : reinterpret_cast<const void*>(sweep_f32_kernel<9, false>);
   else return false;
-  const size_t smem = sweep_f32_smem(ld, S, nsteps);
+  const size_t smem = sweep_f32_smem(ld, S, nsteps, h16);
   int dev = 0, sms = 0, occ = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -874,8 +979,9 @@ bool launch_sweep_f32(int nt, int ld, int T4, int nsteps, const ApplyRow* table,
   e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) {
     const ApplyRow* tb = table;
-    const cf* bl = static_cast<const cf*>(blocks);
-    void* args[] = {(void*)&nt, (void*)&ld, (void*)&T4, (void*)&nsteps, (void*)&tb, (void*)&bl,
+    const void* bl = blocks;
+    const float* bs = bscale;
+    void* args[] = {(void*)&nt, (void*)&ld, (void*)&T4, (void*)&nsteps, (void*)&tb, (void*)&bl, (void*)&bs,
                     (void*)&aux, (void*)&y, (void*)&y32, (void*)&S, (void*)&bar, (void*)&status};
     e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kSweepThreads), args, smem, s);
   }

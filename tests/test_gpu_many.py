@@ -2,8 +2,10 @@
 
 Each instance has its own medium, grid, layer count and sources; solving
 them together must give exactly what solving each alone gives (the same
-kernels on the same data, only overlapped in time), and each must match the
-oracle's global direct solve within the mixed tolerance.
+kernels on the same data, only overlapped in time: the concurrent contexts
+take the per-step preconditioner sweeps, so the single solves are asked for
+them too), and each must match the oracle's global direct solve within the
+mixed tolerance.
 """
 import numpy as np
 import pytest
@@ -21,7 +23,7 @@ def _rel(a, b):
 
 
 def test_uneven_batch_equals_single_solves_and_oracle():
-    from paper_1410_5910_gb300 import PT_MIXED_FP32, PolarTrace, solve_many
+    from paper_1410_5910_gb300 import PT_MIXED_FP32, PT_OPT_SWEEP, PolarTrace, solve_many
 
     cases = W.uneven_batch(count=4, seed=7, nmin=21, nmax=41, Lmin=3, Lmax=5, npml=8, smax=3)
     solvers, fs, refs = [], [], []
@@ -38,6 +40,7 @@ def test_uneven_batch_equals_single_solves_and_oracle():
     assert len({(wl.nx, wl.L, len(wl.sources)) for wl in cases}) > 1  # really uneven
     us, its, rels = solve_many(solvers, fs, tol=1e-9)
     for k, (sv, f, wl) in enumerate(zip(solvers, fs, cases)):
+        sv.set_option(PT_OPT_SWEEP, 1)
         u1, _, it1, rel1 = sv.solve(f, tol=1e-9)
         torch.cuda.synchronize()
         assert torch.equal(us[k], u1) and its[k] == it1

@@ -140,13 +140,17 @@ def test_mixed_local_solve_variants_match_oracle(small, variant, tol_field):
 @pytest.mark.parametrize("nsrc", [1, 3])
 def test_one_launch_sweeps_match_per_step_sweeps_and_oracle(small, nsrc):
     """The FP32 preconditioner with all sweep steps in one cooperative launch (default) against one launch
-    per step (the same products in the same order) and against Algorithm 4 of the oracle."""
-    from paper_1410_5910_gb300 import PT_OPT_SWEEP
+    per step (the same products in the same order) and against Algorithm 4 of the oracle; the FP16 one
+    (PT_OPT_PRECOND_FP16) against the oracle at its own accuracy."""
+    from paper_1410_5910_gb300 import PT_OPT_PRECOND_FP16, PT_OPT_SWEEP
 
     wl, prob, _, off = small
     _, solver = _mk(wl, precision=1, max_sources=nsrc)
     x = _rand_vec(solver, 5, nsrc)
     xt = torch.from_numpy(x).cuda()
+    solver.set_option(PT_OPT_PRECOND_FP16, 1)
+    half = solver.precond(xt).cpu().numpy()
+    solver.set_option(PT_OPT_PRECOND_FP16, 0)
     fused = solver.precond(xt).cpu().numpy()
     solver.set_option(PT_OPT_SWEEP, 1)
     stepped = solver.precond(xt).cpu().numpy()
@@ -157,6 +161,7 @@ def test_one_launch_sweeps_match_per_step_sweeps_and_oracle(small, nsrc):
         unperm[sp_.perm] = x[q]
         ref = polarized.gauss_seidel_preconditioner(sp_, unperm.ravel(), 2)
         assert _rel(fused[q].ravel(), ref) < 1e-5
+        assert _rel(half[q].ravel(), ref) < 1e-2
     # and a whole solve with each
     f = wl.f()
     solver.set_option(PT_OPT_SWEEP, 0)
@@ -169,19 +174,26 @@ def test_one_launch_sweeps_match_per_step_sweeps_and_oracle(small, nsrc):
 
 @pytest.mark.parametrize("nsrc", [1, 3])
 def test_mixed_working_operators_match_oracle(small, nsrc):
-    """The operators PT_MIXED_FP32 iterates with: double-float P M (~1e-14), FP32 R and D^{-1} (~1e-7), against
-    the oracle's FP64 operators."""
+    """The operators PT_MIXED_FP32 iterates with: double-float P M (~1e-14); R and D^{-1} with the FP32 blocks
+    (default, ~1e-7) and with the row-scaled FP16 blocks (option, ~1e-4), against the oracle's FP64 operators."""
+    from paper_1410_5910_gb300 import PT_OPT_PRECOND_FP16
+
     wl, prob, _, off = small
     _, solver = _mk(wl, precision=1, max_sources=nsrc)
     x = _rand_vec(solver, 21, nsrc)
     xt = torch.from_numpy(x).cuda()
     sp_ = off.split
+    solver.set_option(PT_OPT_PRECOND_FP16, 1)
+    half = {w: solver.apply(w, xt, working=True).cpu().numpy() for w in ("R", "Dinv")}
+    solver.set_option(PT_OPT_PRECOND_FP16, 0)
     got = {w: solver.apply(w, xt, working=True).cpu().numpy() for w in ("matvec", "R", "Dinv")}
     for q in range(nsrc):
         xs = x[q].ravel()
         assert _rel(got["matvec"][q].ravel(), sp_.PM.apply(xs)) < 1e-12
         assert _rel(got["R"][q].ravel(), sp_.apply_R(xs)) < 2e-6
         assert _rel(got["Dinv"][q].ravel(), sp_.solve_D(xs)) < 2e-6
+        assert _rel(half["R"][q].ravel(), sp_.apply_R(xs)) < 5e-3
+        assert _rel(half["Dinv"][q].ravel(), sp_.solve_D(xs)) < 1e-2
 
 
 @pytest.mark.parametrize("sources", [((100, 60),), ((7, 3), (190, 110), (60, 95))])
@@ -229,6 +241,26 @@ def test_relaxed_matvecs_keep_the_tolerance(tol):
         assert abs(its1[q] - its0[q]) <= 1
         assert _rel(u1[q].cpu().numpy(), u0[q].cpu().numpy()) < 1e-5
         assert _rel(u1[q].cpu().numpy(), ref[q]) < max(1e-5, 10 * tol)
+
+
+def test_fp16_preconditioner_keeps_iterations_and_tolerance():
+    """The FP16 preconditioner blocks (option) against the FP32 ones on a 200 x 120 grid with 13-17 column chunks:
+    both solves reach the tolerance, with at most two more iterations, and the same field."""
+    from paper_1410_5910_gb300 import PT_OPT_PRECOND_FP16
+
+    wl = W.small_case(200, 120, 10, 4, medium="grf", seed=9, sources=((50, 40), (150, 90)))
+    prob, solver = _mk(wl, precision=1, max_sources=2)
+    ft = torch.from_numpy(wl.f()).cuda()
+    solver.set_option(PT_OPT_PRECOND_FP16, 1)
+    u16, _, its16, rel16 = solver.solve(ft, tol=1e-8)
+    solver.set_option(PT_OPT_PRECOND_FP16, 0)
+    u32, _, its32, rel32 = solver.solve(ft, tol=1e-8)
+    ref = S.global_solve(prob, wl.f())
+    for q in range(2):
+        assert rel16[q] <= 1e-8 and rel32[q] <= 1e-8
+        assert its16[q] <= its32[q] + 2
+        assert _rel(u16[q].cpu().numpy(), u32[q].cpu().numpy()) < 1e-5
+        assert _rel(u16[q].cpu().numpy(), ref[q]) < 1e-5
 
 
 def test_batched_sources_equal_single_solves():
