@@ -97,3 +97,27 @@ def test_create_rejects_null_and_small_workspace_without_touching_the_gpu(L):
     assert L.pt_create(C.byref(p), C.c_void_p(256), C.c_void_p(256), 16, C.c_void_p(512), 16, None,
                        C.byref(ctx)) == 2
     assert not ctx.value
+
+
+def test_mixed_form_workspace_holds_its_copies_and_chunk_transfer_matrices(L):
+    """Host-side sizes of the mixed FP32 form: the persistent workspace grows by at least the complex64 hi / lo
+    and FP16 block copies and the chunk transfer matrices (K_r + K_v chunks per layer, three n x n complex64
+    matrices each); the setup workspace holds the FP64 scratch the transfer matrices are formed in."""
+    nx, nz, npml, L_ = 128, 128, 10, 4
+    nt = nx + 2 * npml
+    ld32 = (nt + 3) & ~3
+    starts = D.layer_partition(nz + 2 * npml, L_)
+    nloc = [int(starts[l + 1] - starts[l]) + (npml if l > 0 else 0) + (npml if l < L_ - 1 else 0) for l in range(L_)]
+    nmax = max(nloc)
+    kmax = max(1, min(64, nt // 16))
+    kr = min(kmax, 32)
+    a64, a32, s32 = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    assert L.pt_workspace_size(C.byref(_params(L, precision=0)), C.byref(a64), None, None) == 0
+    assert L.pt_workspace_size(C.byref(_params(L, precision=1)), C.byref(a32), C.byref(s32), None) == 0
+    copies = L_ * 16 * nt * ld32 * (8 + 8 + 4)
+    # K_v is at least 1 and at most kmax (it depends on the SM count of the device, if there is one)
+    transfer_min = L_ * (kr + 1) * 3 * nmax * nmax * 8
+    assert a32.value - a64.value >= copies + transfer_min
+    assert s32.value >= L_ * kr * 4 * nmax * nmax * 16
+    # options are per context: a NULL context is an argument error, not a crash
+    assert L.pt_set_option(None, 6, 1) == 1
