@@ -201,7 +201,8 @@ pt_status pt_rhs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y, void* 
  *   Set-up: the first call on a device, with that device current, looks up
  *   the array's device address once (cudaGetSymbolAddress) and caches it;
  *   make that first call before any stream capture.  The device current at
- *   every call must be the one the context was created on.
+ *   every call must be the one the context was created on; otherwise the
+ *   call returns PT_ERR_ARG before any lookup or launch.
  *   Sharing: every call uses the same array and leaves its contents behind;
  *   a call writes every byte it reads, so nothing needs clearing, but calls
  *   that overlap on the GPU (other streams, other threads) race on the array.
@@ -214,8 +215,11 @@ pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* y
  * operator, as pt_apply_matvec / pt_apply_R / pt_apply_D_inverse);
  * working = 1: what pt_solve uses for it - the partitioned low-rank blocks
  * when the context compresses (plr = 1), FP32 blocks for R and D^{-1} in the
- * mixed precision, double-float for P M in the mixed precision.  x and y are
- * device trace vectors (nsrc of them), scratch >= solve_bytes. */
+ * mixed precision, double-float for P M in the mixed precision.  which = 3:
+ * P M in the arithmetic of the explicit residual that pt_solve forms between
+ * restart cycles (double-float in the mixed forms with dense blocks, FP64
+ * otherwise; working is ignored).  x and y are device trace vectors (nsrc of
+ * them), scratch >= solve_bytes. */
 pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32_t nsrc, const pt_c128* x, pt_c128* y,
                    void* scratch, size_t scratch_bytes);
 

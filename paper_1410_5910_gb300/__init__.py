@@ -194,9 +194,10 @@ class PolarTrace:
         return torch.empty((S, self.T4, self.nt), dtype=torch.complex128, device=self.device)
 
     def apply(self, which: str, x: torch.Tensor, working: bool = True) -> torch.Tensor:
-        """One operator ('matvec', 'R', 'Dinv') in the solver's working representation (or dense FP64)."""
+        """One operator ('matvec', 'R', 'Dinv') in the solver's working representation (or dense FP64);
+        'restart': P M in the arithmetic of the explicit residual between restart cycles."""
         y = torch.empty_like(x)
-        w = {"matvec": 0, "R": 1, "Dinv": 2}[which]
+        w = {"matvec": 0, "R": 1, "Dinv": 2, "restart": 3}[which]
         check(lib().pt_apply(self._ctx, w, int(working), x.shape[0], _ptr(x), _ptr(y), _ptr(self._scratch),
                              self._scratch.numel()), "pt_apply")
         return y

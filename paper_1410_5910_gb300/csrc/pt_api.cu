@@ -720,6 +720,7 @@ struct pt_ctx {
   int opt_learned = 0;      // PT_OPT_LEARNED
   int learned_used = 0;     // cycles of the last solve that applied the correction
   int last_cycles = 0;      // restart cycles (explicit residuals) of the last solve
+  int device = -1;          // the CUDA device current at pt_create
 };
 
 static const char* kStatusText[] = {"ok", "invalid argument", "workspace too small", "CUDA error",
@@ -907,6 +908,7 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   if (!c) return fail(PT_ERR_ARG, "host allocation failed");
   c->prm = *prm;
   c->P = P;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return fail(PT_ERR_CUDA, "cudaGetDevice"); }
   c->stream = static_cast<cudaStream_t>(stream);
   c->d = carve_persist(P, prm, persistent, nullptr);
   if (c->d.chunk_T) c->opt_local_solve = 4;  // mixed FP32: chunked local solves by default
@@ -1113,6 +1115,16 @@ cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y, bool exact = true) {
   return apply(c, mode, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, true);
 }
 
+// y = P M x in the arithmetic of the explicit residual between restart cycles (iterative
+// refinement): FP64 blocks in PT_FP64 and with compressed blocks; in the mixed forms the
+// double-float product (~1e-14) on the FP32 pipes (the FP64 pipe bounds an FP64 product at
+// about twice its time), which in PT_MIXED_TC also corrects the ~1e-5 tensor-core matvec of
+// the inner cycles
+cudaError_t do_restart_matvec(pt_ctx* c, int S, const cd* x, cd* y) {
+  if (mixed(c) && !c->P.plr) return apply(c, kModeDF, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, false);
+  return do_matvec(c, S, x, y);
+}
+
 // y = alpha R x + beta aux
 cudaError_t do_R(pt_ctx* c, int S, const cd* x, cd* y, int mode, double alpha = 1.0, double beta = 0.0,
                  const cd* aux = nullptr, bool working = false) {
@@ -1154,8 +1166,8 @@ cudaError_t do_Dinv(pt_ctx* c, int S, const cd* r, cd* y, int mode, bool working
 
 // Algorithm 4: z = D^{-1} r; repeat n_it - 1 times z = D^{-1}(r - R z).
 // Mixed form: FP32 blocks (the preconditioner only has to be approximate in flexible GMRES).
-// the arithmetic of the preconditioner's products: FP16 blocks (mixed FP32 form, by default),
-// FP32 blocks, the tensor cores, or FP64
+// the arithmetic of the preconditioner's products: FP16 blocks when PT_OPT_PRECOND_FP16 is set
+// (mixed FP32 form), otherwise complex64 blocks in the mixed FP32 form, the tensor cores, or FP64
 int precond_mode(const pt_ctx* c) {
   if (tcmode(c)) return kModeTC1;
   if (!mixed(c)) return kModeFP64;
@@ -1232,7 +1244,7 @@ extern "C" pt_status pt_apply_matvec(pt_ctx* ctx, int32_t nsrc, const pt_c128* x
 
 extern "C" pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32_t nsrc, const pt_c128* x,
                               pt_c128* y, void* scratch, size_t scratch_bytes) {
-  if (!ctx || !x || !y || x == y || which < 0 || which > 2) return fail(PT_ERR_ARG, "bad arguments");
+  if (!ctx || !x || !y || x == y || which < 0 || which > 3) return fail(PT_ERR_ARG, "bad arguments");
   size_t need = 0;
   carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
   pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
@@ -1245,6 +1257,8 @@ extern "C" pt_status pt_apply(pt_ctx* ctx, int32_t which, int32_t working, int32
   const bool w = working != 0;
   if (which == 0) {
     PT_CUDA(do_matvec(ctx, nsrc, xd, yd, !w));
+  } else if (which == 3) {
+    PT_CUDA(do_restart_matvec(ctx, nsrc, xd, yd));
   } else {
     const int mode = w ? precond_mode(ctx) : kModeFP64;
     if (which == 1) PT_CUDA(do_R(ctx, nsrc, xd, yd, mode, 1.0, 0.0, nullptr, w));
@@ -1800,13 +1814,8 @@ static pt_status solve_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, do
     PT_CUDA(cudaMemcpyAsync(B.kk, kk.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
     c->launches += 2;
     PT_CUDA(launch_lsq_combine(S, m, B.kk, B.H, B.g, B.y, B.Z, N, B.x, s));
-    // explicit residual r = P b - P M x between restart cycles (iterative refinement): FP64 blocks
-    // in PT_FP64 and with compressed blocks; in the mixed forms the double-float product (~1e-14)
-    // on the FP32 pipes (the FP64 pipe bounds an FP64 product at about twice its time), which in
-    // PT_MIXED_TC also corrects the ~1e-5 tensor-core matvec of the inner cycles
-    if (mixed(c) && !c->P.plr)
-      PT_CUDA(apply(c, kModeDF, op_matvec(c), S, B.x, nullptr, B.t, kApplyRowsWide, 1.0, 0.0, false));
-    else PT_CUDA(do_matvec(c, S, B.x, B.t));
+    // explicit residual r = P b - P M x between restart cycles (iterative refinement)
+    PT_CUDA(do_restart_matvec(c, S, B.x, B.t));
     c->launches += 2;
     PT_CUDA(launch_sub(B.b, B.t, B.w, S * N, s));
     PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, reinterpret_cast<double*>(B.partial),
@@ -1935,9 +1944,11 @@ static __device__ __align__(256) unsigned char g_rhs_noalloc_scratch[kRhsNoalloc
 
 // Device address of the array on the current device; the first call on a
 // device performs the lookup (cudaGetSymbolAddress) with that device current.
-static pt_status rhs_noalloc_scratch(void** out) {
+static pt_status rhs_noalloc_scratch(const pt_ctx* ctx, void** out) {
   int dev = -1;
   PT_CUDA(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return fail(PT_ERR_ARG, "pt_rhs_noalloc: the current device is not the device the context was created on");
   if (dev < 0 || dev >= kNoallocMaxDevices) return fail(PT_ERR_ARG, "pt_rhs_noalloc: device index out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_addr[dev]) {
@@ -1962,7 +1973,7 @@ extern "C" pt_status pt_rhs_noalloc(pt_ctx* ctx, int32_t nsrc, const pt_c128* f,
     return fail(PT_ERR_WORKSPACE, "pt_rhs_noalloc: needs " + std::to_string(need) +
                                       " bytes, more than its 16 MiB built-in scratch; use pt_rhs");
   void* base = nullptr;
-  pt_status st = rhs_noalloc_scratch(&base);
+  pt_status st = rhs_noalloc_scratch(ctx, &base);
   if (st != PT_OK) return st;
   cd* Y = static_cast<cd*>(base);
   int* flag = reinterpret_cast<int*>(static_cast<char*>(base) + ybytes);

@@ -532,7 +532,9 @@ __global__ void blocks_h16_kernel(const cd* __restrict__ src, int nt, int ld, si
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     int ex = 0;
     if (m > 0.0) frexp(m, &ex);  // m in [2^(ex-1), 2^ex)
-    const int p = m > 0.0 ? 14 - ex : 0;
+    // the scale 2^-p is stored as a float: p stays in [-127, 126] so that it is a normal
+    // number; a row whose largest entry is below 2^-112 then keeps fewer FP16 bits
+    const int p = m > 0.0 ? max(-127, min(126, 14 - ex)) : 0;
     const double mult = ldexp(1.0, p);
     for (int k = lane; k < ld; k += 32) {
       float2 v = make_float2(0.f, 0.f);

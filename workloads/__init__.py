@@ -56,10 +56,10 @@ def layered_medium(nt: int, Nz: int, seed: int, n_interfaces: int = 12, cmin: fl
     x = np.arange(nt, dtype=np.float64)
     z = np.arange(Nz, dtype=np.float64)
     depths = np.sort(g.uniform(0.05, 0.95, n_interfaces)) * Nz
-    # interfaces z_k(x) = mean depth + 3 random sinusoids, amplitudes <= 3% of depth
+    # interfaces z_k(x) = mean depth + 3 random sinusoids, each amplitude <= 3% of depth
     surf = np.empty((n_interfaces, nt))
     for k, d in enumerate(depths):
-        amp = g.uniform(0.0, 0.01, 3) * d
+        amp = g.uniform(0.0, 0.03, 3) * d
         wl = g.uniform(0.2, 1.0, 3) * nt
         ph = g.uniform(0, 2 * np.pi, 3)
         surf[k] = d + np.sum(amp[:, None] * np.sin(2 * np.pi * x[None, :] / wl[:, None] + ph[:, None]), axis=0)
@@ -96,6 +96,15 @@ def point_sources(nt: int, Nz: int, npml: int, h: float, positions) -> np.ndarra
     for s, (p, q) in enumerate(pos):
         f[s, q - 1 + npml, p - 1 + npml] = 1.0 / (h * h)
     return f
+
+
+def point_source_entries(npml: int, h: float, positions):
+    """The nonzero entries of ``point_sources``: (rows, cols, value) with rows / cols the extended-grid
+    indices of each source's node and value = 1/h^2, for building large batches in place."""
+    pos = list(positions)
+    rows = [q - 1 + npml for _, q in pos]
+    cols = [p - 1 + npml for p, _ in pos]
+    return rows, cols, 1.0 / (h * h)
 
 
 def random_sources(nt: int, Nz: int, npml: int, nx: int, nz: int, seed: int, count: int) -> np.ndarray:
