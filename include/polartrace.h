@@ -105,10 +105,20 @@ typedef struct {
   int32_t learned;    /* 1: reserve the solve-scratch buffers of the learned
                          preconditioner correction (pt_set_correction,
                          PT_OPT_LEARNED); 0: none                                    */
+  const int32_t* layer_rows; /* host, L ints or NULL.  The rows n^l of each layer (Section
+                         2.2 allows any increasing sequence of interfaces): layer l
+                         covers the extended-grid rows row_start[l] ..
+                         row_start[l] + n^l - 1, the sum must be N_z = nz + 2 npml,
+                         every n^l >= 3, and no interface may lie in or next to the
+                         PML (npml + 1 <= row_start[l] <= N_z - npml - 1 for l >= 1).
+                         NULL: the near-equal split of pt_layer_partition.  Read
+                         only during the call it is passed to (pt_create copies
+                         the partition).                                             */
 } pt_params;
 
-/* Layer partition used by the library (Section 2.2): the first (N_z mod L)
- * layers get one extra row.  row_start must hold L+1 ints (host); on return
+/* Layer partition used by the library (Section 2.2): layer_rows when given,
+ * otherwise the near-equal split in which the first (N_z mod L) layers get
+ * one extra row.  row_start must hold L+1 ints (host); on return
  * row_start[l] is the first extended-grid row of layer l and row_start[L] = N_z.
  * Fails with PT_ERR_ARG when an interface would lie within one row of the
  * PML or a layer would have fewer than 3 rows. */
@@ -157,6 +167,23 @@ pt_status pt_create(const pt_params* prm, const double* c_ext, void* persistent,
  * not reach rel_tol within max_it iterations. */
 pt_status pt_solve(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* u, pt_c128* traces, double rel_tol,
                    int32_t max_it, void* scratch, size_t scratch_bytes, int32_t* iters, double* relres);
+
+/* Gauss-Seidel iteration used as a solver (Algorithm 3, Section 4.1) on the
+ * permuted polarized jump system:  u^0 = 0,
+ *     u^{k+1} = D^{-1} (P b - R u^k),
+ * stopping when ||u^{k+1} - u^k|| / ||u^k|| <= rel_tol for every source (the
+ * test of Algorithm 3, per source) or after max_it iterations; then the
+ * volume field is reconstructed as in pt_solve (Algorithm 2).  The sweeps
+ * D^{-1} and the coupling R use the exact FP64 blocks in every precision
+ * form.  Arguments and layouts are those of pt_solve; iters[s] counts the
+ * iterations, relres[s] is the FP64 true relative residual
+ * ||P b - P M u|| / ||P b||.  max_it is not limited by max_krylov.
+ * Returns PT_ERR_NOT_CONVERGED (outputs written) when some source did not
+ * meet the test within max_it iterations; the iteration's convergence
+ * depends on the spectral radius of D^{-1} R (Section 4.2), which exceeds 1
+ * in some media, where only preconditioned GMRES (pt_solve) converges. */
+pt_status pt_solve_gs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* u, pt_c128* traces, double rel_tol,
+                      int32_t max_it, void* scratch, size_t scratch_bytes, int32_t* iters, double* relres);
 
 /* Same as pt_solve with f and u in HOST memory (pinned memory gives the best
  * copy rate); the library copies them through the scratch buffer, whose size

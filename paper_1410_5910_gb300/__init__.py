@@ -28,14 +28,19 @@ def default_pml_strength(c_max: float) -> float:
 
 
 def _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr=0, plr_eps=1e-9,
-            plr_rmax=24, learned=0) -> Params:
-    return Params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr, plr_eps,
-                  plr_rmax, learned)
+            plr_rmax=24, learned=0, layer_rows=None):
+    """(pt_params, keep-alive) - the int32 array behind layer_rows must outlive the call that reads it."""
+    rows = None
+    if layer_rows is not None:
+        rows = (C.c_int32 * len(layer_rows))(*[int(v) for v in layer_rows])
+    p = Params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov, plr, plr_eps,
+               plr_rmax, learned, C.cast(rows, C.POINTER(C.c_int32)) if rows is not None else None)
+    return p, rows
 
 
-def layer_partition(nx, nz, npml, L) -> list:
-    """Row offsets of the library's layer split (Section 2.2)."""
-    p = _params(nx, nz, npml, L, 1.0, 1.0, 1.0, PT_FP64, 2, 1, 1)
+def layer_partition(nx, nz, npml, L, layer_rows=None) -> list:
+    """Row offsets of the library's layer split (Section 2.2), or of the given rows per layer."""
+    p, _keep = _params(nx, nz, npml, L, 1.0, 1.0, 1.0, PT_FP64, 2, 1, 1, layer_rows=layer_rows)
     out = (C.c_int32 * (L + 1))()
     check(lib().pt_layer_partition(C.byref(p), out), "pt_layer_partition")
     return list(out)
@@ -86,7 +91,7 @@ class PolarTrace:
     def __init__(self, nx: int, nz: int, npml: int, L: int, h: float, omega: float, c_ext: torch.Tensor,
                  pml_C: float | None = None, precision: int = PT_FP64, gs_iters: int = 2, max_sources: int = 1,
                  max_krylov: int = 40, stream: torch.cuda.Stream | None = None, plr: bool = False,
-                 plr_eps: float = 1e-9, plr_rmax: int = 24, learned: bool = False):
+                 plr_eps: float = 1e-9, plr_rmax: int = 24, learned: bool = False, layer_rows=None):
         if not (c_ext.is_cuda and c_ext.dtype == torch.float64 and c_ext.is_contiguous()):
             raise ValueError("c_ext must be a contiguous float64 CUDA tensor of shape (N_z, n_t)")
         self.nx, self.nz, self.npml, self.L = nx, nz, npml, L
@@ -95,8 +100,8 @@ class PolarTrace:
             raise ValueError(f"c_ext must have shape {(self.Nz, self.nt)}")
         if pml_C is None:
             pml_C = default_pml_strength(float(c_ext.max()))
-        self.params = _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources, max_krylov,
-                              int(plr), plr_eps, plr_rmax, int(learned))
+        self.params, self._rows = _params(nx, nz, npml, L, h, omega, pml_C, precision, gs_iters, max_sources,
+                                          max_krylov, int(plr), plr_eps, plr_rmax, int(learned), layer_rows)
         self.max_sources, self.max_krylov = max_sources, max_krylov
         self.device = c_ext.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -153,6 +158,26 @@ class PolarTrace:
             out_u = out_u[0] if out_u is not None else None
             tr = tr[0] if tr is not None else None
         return out_u, tr, list(iters), list(rel)
+
+    def solve_gs(self, f: torch.Tensor, tol: float = 1e-7, max_it: int = 200, want_u: bool = True,
+                 want_traces: bool = True, allow_not_converged: bool = False):
+        """Algorithm 3 (Gauss-Seidel iteration as the solver) for S sources.  Returns (u, traces, iterations,
+        FP64 true relative residuals of the polarized system)."""
+        squeeze = f.dim() == 2
+        if squeeze:
+            f = f.unsqueeze(0)
+        S = self._check_src(f)
+        u = torch.empty_like(f) if want_u else None
+        tr = torch.empty((S, self.T4, self.nt), dtype=torch.complex128, device=self.device) if want_traces else None
+        iters = (C.c_int32 * S)()
+        rel = (C.c_double * S)()
+        st = lib().pt_solve_gs(self._ctx, S, _ptr(f), _ptr(u) if want_u else None, _ptr(tr) if want_traces else None,
+                               tol, max_it, _ptr(self._scratch), self._scratch.numel(), iters, rel)
+        check(st, "pt_solve_gs", allow=(5,) if allow_not_converged else ())
+        if squeeze:
+            u = u[0] if u is not None else None
+            tr = tr[0] if tr is not None else None
+        return u, tr, list(iters), list(rel)
 
     def host_scratch_bytes(self) -> int:
         return self.solve_bytes + 2 * self.max_sources * self.Nz * self.nt * 16 + 4096

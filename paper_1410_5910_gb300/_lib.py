@@ -25,6 +25,7 @@ EXPORTS = [
     "pt_volume_residual", "pt_set_option", "pt_correction_nparams", "pt_set_correction", "pt_get_correction",
     "pt_correction_scratch_bytes", "pt_correction_forward", "pt_correction_grad", "pt_train_bytes",
     "pt_train_correction", "pt_apply_correction", "pt_last_solve_cycles", "pt_solve_many", "pt_last_solve_relaxed",
+    "pt_solve_gs",
 ]
 PT_OPT_LAYER_GROUP = 1
 PT_OPT_LEARNED = 2
@@ -40,6 +41,7 @@ class Params(C.Structure):
         ("h", C.c_double), ("omega", C.c_double), ("pml_C", C.c_double),
         ("precision", C.c_int32), ("gs_iters", C.c_int32), ("max_sources", C.c_int32), ("max_krylov", C.c_int32),
         ("plr", C.c_int32), ("plr_eps", C.c_double), ("plr_rmax", C.c_int32), ("learned", C.c_int32),
+        ("layer_rows", C.POINTER(C.c_int32)),
     ]
 
 
@@ -67,6 +69,7 @@ def lib() -> C.CDLL:
     L.pt_workspace_size.argtypes = [P, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     L.pt_create.argtypes = [P, vp, vp, sz, vp, sz, vp, C.POINTER(vp)]
     L.pt_solve.argtypes = [vp, i32, vp, vp, vp, f64, i32, vp, sz, C.POINTER(i32), C.POINTER(f64)]
+    L.pt_solve_gs.argtypes = [vp, i32, vp, vp, vp, f64, i32, vp, sz, C.POINTER(i32), C.POINTER(f64)]
     L.pt_solve_host.argtypes = [vp, i32, vp, vp, f64, i32, vp, sz, C.POINTER(i32), C.POINTER(f64)]
     for name in ("pt_apply_matvec", "pt_apply_D_inverse", "pt_apply_R"):
         getattr(L, name).argtypes = [vp, i32, vp, vp]

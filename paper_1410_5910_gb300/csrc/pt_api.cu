@@ -204,14 +204,20 @@ pt_status make_plan(const pt_params* p, Plan& P) {
   }
   P.ld32 = (P.nt + 3) & ~3;
   P.g = Geometry{P.nt, P.Nz, p->npml, P.L, p->h, p->omega, p->pml_C};
-  // near-equal split: the first (N_z mod L) layers get one extra row
+  // the caller's rows per layer, or the near-equal split: the first (N_z mod L) layers get one
+  // extra row
   const int base = P.Nz / P.L, extra = P.Nz % P.L;
+  if (p->layer_rows) {
+    long long sum = 0;
+    for (int l = 0; l < P.L; ++l) sum += p->layer_rows[l];
+    if (sum != P.Nz) return fail(PT_ERR_ARG, "layer_rows must sum to N_z = nz + 2 npml");
+  }
   int start = 0;
   P.layers.resize(P.L);
   for (int l = 0; l < P.L; ++l) {
     LayerInfo& I = P.layers[l];
     I.start = start;
-    I.n = base + (l < extra ? 1 : 0);
+    I.n = p->layer_rows ? p->layer_rows[l] : base + (l < extra ? 1 : 0);
     start += I.n;
     I.has_top = l > 0;
     I.has_bot = l < P.L - 1;
@@ -224,7 +230,7 @@ pt_status make_plan(const pt_params* p, Plan& P) {
     I.row[3] = I.has_bot ? I.pad_top + I.n : -1;
     if (I.n < 3) return fail(PT_ERR_ARG, "every layer needs at least 3 rows");
     if (l > 0 && !(I.start >= p->npml + 1 && I.start <= P.Nz - p->npml - 1))
-      return fail(PT_ERR_ARG, "an interface lies in or next to the PML; use fewer layers");
+      return fail(PT_ERR_ARG, "an interface lies in or next to the PML; use fewer or other layers");
     P.nloc_max = std::max(P.nloc_max, I.nloc);
     I.sinv_off = (long long)P.sinv_elems;
     I.coef_off = (long long)P.coef_elems;
@@ -907,6 +913,7 @@ extern "C" pt_status pt_create(const pt_params* prm, const double* c_ext, void* 
   pt_ctx* c = new (std::nothrow) pt_ctx();
   if (!c) return fail(PT_ERR_ARG, "host allocation failed");
   c->prm = *prm;
+  c->prm.layer_rows = nullptr;  // the partition lives in the plan; the caller's array is not kept
   c->P = P;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return fail(PT_ERR_CUDA, "cudaGetDevice"); }
   c->stream = static_cast<cudaStream_t>(stream);
@@ -1869,6 +1876,92 @@ extern "C" pt_status pt_solve(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c1
   SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
   return solve_impl(ctx, nsrc, reinterpret_cast<const cd*>(f), reinterpret_cast<cd*>(u),
                     reinterpret_cast<cd*>(traces), rel_tol, max_it, B, iters, relres);
+}
+
+// ---- Gauss-Seidel iteration as a solver (Algorithm 3, Section 4.1) -----------
+// u^0 = 0; u^{k+1} = D^{-1}(P b - R u^k) while ||u^{k+1} - u^k|| / ||u^k|| > tol, with the
+// exact FP64 operators in every precision form (the iteration converges to the accuracy of
+// the operators it applies); then the FP64 true residual and the reconstruction of pt_solve.
+static pt_status solve_gs_impl(pt_ctx* c, int S, const cd* f, cd* u, cd* traces, double tol, int max_it,
+                               const SolveBufs& B, int32_t* iters_out, double* relres_out) {
+  const size_t N = c->P.N;
+  cudaStream_t s = c->stream;
+  c->launches = 0;
+  {
+    pt_status bs = bind_call(c, B, S);
+    if (bs != PT_OK) return bs;
+  }
+  std::vector<double> nrm_old(S, 0.0), nrm_new(S), nrm_diff(S);
+  std::vector<int> done(S, 0), its(S, 0);
+  PT_CUDA(cudaMemsetAsync(c->d.status, 0, sizeof(int), s));
+  PT_CUDA(do_rhs(c, S, f, B.b, B));  // P b
+  PT_CUDA(cudaMemsetAsync(B.x, 0, S * N * sizeof(cd), s));
+  double* partial = reinterpret_cast<double*>(B.partial);
+  for (int k = 1; k <= max_it; ++k) {
+    PT_CUDA(do_R(c, S, B.x, B.t, kModeFP64, -1.0, 1.0, B.b, false));  // t = P b - R u^k
+    PT_CUDA(do_Dinv(c, S, B.t, B.u1, kModeFP64, false));              // u^{k+1} = D^{-1} t
+    c->launches += 3;
+    PT_CUDA(launch_sub(B.u1, B.x, B.w, S * N, s));
+    PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, partial, s));
+    PT_CUDA(cudaMemcpyAsync(nrm_diff.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PT_CUDA(launch_norm_scale(B.u1, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, partial, s));
+    PT_CUDA(cudaMemcpyAsync(nrm_new.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // sources that have converged keep their iterate: copy only the active ones
+    for (int q = 0; q < S; ++q)
+      if (!done[q])
+        PT_CUDA(cudaMemcpyAsync(B.x + (size_t)q * N, B.u1 + (size_t)q * N, N * sizeof(cd), cudaMemcpyDeviceToDevice,
+                                s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int q = 0; q < S; ++q) {
+      if (done[q]) continue;
+      its[q] = k;
+      const bool zero = nrm_new[q] == 0.0 && nrm_diff[q] == 0.0;  // a zero source: u = 0 is exact
+      if (zero || (nrm_old[q] > 0.0 && nrm_diff[q] <= tol * nrm_old[q])) done[q] = 1;
+      else all = false;
+      nrm_old[q] = nrm_new[q];
+    }
+    if (all) break;
+  }
+  // FP64 true residual ||P b - P M u|| / ||P b||
+  PT_CUDA(do_matvec(c, S, B.x, B.t));
+  c->launches += 3;
+  PT_CUDA(launch_sub(B.b, B.t, B.w, S * N, s));
+  std::vector<double> rn(S), bn(S);
+  PT_CUDA(launch_norm_scale(B.w, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, partial, s));
+  PT_CUDA(cudaMemcpyAsync(rn.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(launch_norm_scale(B.b, N, S, B.nrm, nullptr, 0, 0, 0, 0, nullptr, 0, partial, s));
+  PT_CUDA(cudaMemcpyAsync(bn.data(), B.nrm, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (traces) PT_CUDA(cudaMemcpyAsync(traces, B.x, S * N * sizeof(cd), cudaMemcpyDeviceToDevice, s));
+  if (u) PT_CUDA(do_layer_solve(c, 1, S, f, B.x, u, B));
+  PT_CUDA(cudaStreamSynchronize(s));
+  pt_status st = read_status(c);
+  if (st != PT_OK) return st;
+  bool conv = true;
+  int maxit = 0;
+  for (int q = 0; q < S; ++q) {
+    if (iters_out) iters_out[q] = its[q];
+    if (relres_out) relres_out[q] = bn[q] > 0.0 ? rn[q] / bn[q] : 0.0;
+    maxit = std::max(maxit, its[q]);
+    if (!done[q]) conv = false;
+  }
+  c->last_max_it = maxit;
+  if (!conv) return fail(PT_ERR_NOT_CONVERGED, "Gauss-Seidel reached max_it before rel_tol");
+  return PT_OK;
+}
+
+extern "C" pt_status pt_solve_gs(pt_ctx* ctx, int32_t nsrc, const pt_c128* f, pt_c128* u, pt_c128* traces,
+                                 double rel_tol, int32_t max_it, void* scratch, size_t scratch_bytes, int32_t* iters,
+                                 double* relres) {
+  if (!ctx || !f) return fail(PT_ERR_ARG, "ctx or f is NULL");
+  if (!(rel_tol > 0) || max_it < 1) return fail(PT_ERR_ARG, "rel_tol > 0 and max_it >= 1 required");
+  size_t need = 0;
+  carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, nullptr, &need);
+  pt_status st = check_solve_args(ctx, nsrc, scratch, scratch_bytes, need);
+  if (st != PT_OK) return st;
+  SolveBufs B = carve_solve(ctx->P, ctx->prm.max_sources, ctx->prm.max_krylov, false, scratch, nullptr);
+  return solve_gs_impl(ctx, nsrc, reinterpret_cast<const cd*>(f), reinterpret_cast<cd*>(u),
+                       reinterpret_cast<cd*>(traces), rel_tol, max_it, B, iters, relres);
 }
 
 extern "C" pt_status pt_solve_many(int32_t nctx, pt_ctx* const* ctxs, const int32_t* nsrc, const pt_c128* const* f,

@@ -121,3 +121,25 @@ def test_mixed_form_workspace_holds_its_copies_and_chunk_transfer_matrices(L):
     assert s32.value >= L_ * kr * 4 * nmax * nmax * 16
     # options are per context: a NULL context is an argument error, not a crash
     assert L.pt_set_option(None, 6, 1) == 1
+
+
+def test_layer_rows_set_the_partition_and_are_validated(L):
+    """Section 2.2 allows any increasing sequence of interfaces: pt_params.layer_rows gives the rows per
+    layer; the library must use exactly that split and reject sums other than N_z, layers under 3 rows
+    and interfaces in or next to the PML, before touching the GPU."""
+    nz, npml, L_ = 128, 10, 4
+    Nz = nz + 2 * npml
+    rows = [50, 22, 41, Nz - 113]
+    arr = (C.c_int32 * L_)(*rows)
+    p = _params(L, nz=nz, npml=npml, L=L_, layer_rows=C.cast(arr, C.POINTER(C.c_int32)))
+    out = (C.c_int32 * (L_ + 1))()
+    assert L.pt_layer_partition(C.byref(p), out) == 0
+    assert list(out) == [0, 50, 72, 113, Nz]
+    assert L.pt_workspace_size(C.byref(p), None, None, None) == 0
+    for bad in ([50, 22, 41, Nz - 112],      # sum N_z + 1
+                [50, 2, 61, Nz - 113],       # a layer of 2 rows
+                [10, 62, 41, Nz - 113],      # first interface at row 10 = inside the 10-row PML
+                [50, 22, Nz - 82, 10]):      # last interface at row 138 > N_z - npml - 1 = 137
+        arr_b = (C.c_int32 * L_)(*bad)
+        pb = _params(L, nz=nz, npml=npml, L=L_, layer_rows=C.cast(arr_b, C.POINTER(C.c_int32)))
+        assert L.pt_layer_partition(C.byref(pb), out) == 1, bad
