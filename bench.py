@@ -482,15 +482,14 @@ def headline_section(args, dev, pg, pk, oracle, world):
                "algorithmic_flops": cplx_mv, "executed_tflops": 3 * cplx_mv / t_mv / 1e12, "launch_ms": t_mv * 1e3,
                "flops_per_unit": "8 n_t^2 real flops per block term and source (one pass of the complex product)",
                "peak_source": "measured bf16 dense burst (FP16 runs at the same rate)"}
-    # FP32-pipe peak: 128 FMA lanes per SM per clock, 152 SMs, 2.07 GHz
-    fp32_peak_tinstr = 128 * 152 * 2.070e9 / 1e12
-    df_instr = 4 * 11 * nblocks_mv * wl.nt * wl.nt * S  # 4 real products per complex one, ~11 FP32 instr each
-    roof_rs = {"kernel": "restart product P M x (double-float, FP32 pipes)", "bound": "alu",
-               "achieved": df_instr / t_rs / 1e12, "peak": fp32_peak_tinstr, "unit": "T FP32 instr/s",
-               "frac": df_instr / t_rs / 1e12 / fp32_peak_tinstr, "traffic": None, "launch_ms": t_rs * 1e3,
-               "complex_tflops": cplx_mv / t_rs / 1e12,
-               "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz; ~11 FP32 instructions per real "
-                              "double-float multiply-add"}
+    # split products of the restart residual: 15 slice pairs, each a full real-concatenated product
+    roof_rs = {"kernel": "oz_apply_kernel (restart residual P M x by split products: five 7-bit FP16 slices per "
+                         "operand, 15 slice pairs, exact FP32 accumulation per 512-long K segment)",
+               "bound": "tensor", "achieved": 15 * cplx_mv / t_rs / 1e12, "peak": peak_tc, "unit": "TFLOP/s",
+               "frac": 15 * cplx_mv / t_rs / 1e12 / peak_tc if peak_tc else None, "traffic": None,
+               "launch_ms": t_rs * 1e3, "complex_tflops": cplx_mv / t_rs / 1e12,
+               "flops_per_unit": "15 x 8 n_t^2 executed FP16 MMA flops per block term and source",
+               "peak_source": "measured bf16 dense burst (FP16 runs at the same rate)"}
     cplx_dinv = 8.0 * (16 * (wl.L - 2) + 8) / 2 * wl.nt * wl.nt * S
     roof_dinv = {"kernel": "tc_apply_kernel, one D^-1 (31 sweep steps, one FP16 pass)", "bound": "tensor",
                  "achieved": cplx_dinv / t_dinv / 1e12, "peak": peak_tc, "unit": "TFLOP/s",

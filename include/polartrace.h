@@ -297,6 +297,14 @@ pt_status pt_plr_stats(const pt_ctx* ctx, int64_t* stored_entries, int32_t* leav
  * power of two into FP16 range (plr = 0 only; about 5e-4 relative on the
  * preconditioner's output: half the bytes of every sweep step and R apply,
  * sometimes one more GMRES iteration).
+ * PT_OPT_RESTART: the explicit residual P b - P M x that PT_MIXED_TC forms
+ * between restart cycles (iterative refinement) - 1 = split products on the
+ * tensor cores (default): blocks and inputs cut into five 7-bit integer
+ * slices held exactly in FP16 (Ozaki et al.'s error-free splitting), the 15
+ * slice pairs of weight >= 2^-42 accumulated exactly in FP32 over K segments
+ * of 512 and summed in double-float, ~1e-10 relative to the largest block
+ * entry of a row times the largest input entry of a source; 0 = the
+ * double-float product on the FP32 pipes (~1e-14).
  * PT_ERR_ARG for an unknown option or value. */
 enum {
   PT_OPT_LAYER_GROUP = 1,
@@ -304,7 +312,8 @@ enum {
   PT_OPT_LOCAL_SOLVE = 3,
   PT_OPT_SWEEP = 4,
   PT_OPT_RELAX = 5,
-  PT_OPT_PRECOND_FP16 = 6
+  PT_OPT_PRECOND_FP16 = 6,
+  PT_OPT_RESTART = 7
 };
 pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value);
 

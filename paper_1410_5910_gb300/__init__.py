@@ -16,9 +16,9 @@ import math
 
 import torch
 
-from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, PT_OPT_LEARNED, PT_OPT_LOCAL_SOLVE, PT_OPT_PRECOND_FP16, PT_OPT_RELAX, PT_OPT_SWEEP, Params, PolarTraceError, check, lib
+from ._lib import PT_FP64, PT_MIXED_FP32, PT_MIXED_TC, PT_OPT_LAYER_GROUP, PT_OPT_LEARNED, PT_OPT_LOCAL_SOLVE, PT_OPT_PRECOND_FP16, PT_OPT_RELAX, PT_OPT_RESTART, PT_OPT_SWEEP, Params, PolarTraceError, check, lib
 
-__all__ = ["PolarTrace", "PolarTraceError", "solve_many", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "PT_OPT_LOCAL_SOLVE", "PT_OPT_PRECOND_FP16", "PT_OPT_RELAX", "PT_OPT_SWEEP", "default_pml_strength",
+__all__ = ["PolarTrace", "PolarTraceError", "solve_many", "PT_FP64", "PT_MIXED_FP32", "PT_MIXED_TC", "PT_OPT_LAYER_GROUP", "PT_OPT_LEARNED", "PT_OPT_LOCAL_SOLVE", "PT_OPT_PRECOND_FP16", "PT_OPT_RELAX", "PT_OPT_RESTART", "PT_OPT_SWEEP", "default_pml_strength",
            "layer_partition"]
 
 

@@ -33,6 +33,7 @@ PT_OPT_LOCAL_SOLVE = 3
 PT_OPT_SWEEP = 4
 PT_OPT_RELAX = 5
 PT_OPT_PRECOND_FP16 = 6
+PT_OPT_RESTART = 7
 
 
 class Params(C.Structure):

@@ -105,6 +105,14 @@ cudaError_t launch_givens(int, int, int, cd*, double*, cd*, cd*, double*, cudaSt
 cudaError_t launch_lsq_combine(int, int, const int*, const cd*, const cd*, cd*, const cd*, size_t, cd*,
                                cudaStream_t);
 cudaError_t launch_sub(const cd*, const cd*, cd*, size_t, cudaStream_t);
+int oz_slices();
+int oz_bn();
+cudaError_t launch_oz_blocks(const cd*, size_t, int, int, __half*, int*, cudaStream_t);
+cudaError_t launch_oz_source_exp(const cd*, size_t, int, int*, cudaStream_t);
+cudaError_t launch_oz_stage(const TcKey*, int, const cd*, int, int, int, int, const int*, size_t, __half*,
+                            cudaStream_t);
+cudaError_t launch_oz_apply(const CUtensorMap&, const CUtensorMap&, const TcRow*, int, int, int, int, int, int,
+                            const int*, const int*, const cd*, const cd*, cd*, double, double, int*, cudaStream_t);
 }  // namespace pt
 
 using namespace pt;
@@ -324,6 +332,8 @@ struct Persist {
   // tensor-core form
   __half* tc_ahi;       // [L * 16 * nt][ldtc]
   __half* tc_alo;
+  __half* oz_a;         // split products of the restart residual: kOzP slices of [L * 16 * nt][ldtc]
+  int* oz_e;            // their row exponents [L * 16 * nt]
   TcRow* tcr_mv;
   TcRow* tcr_R;
   TcRow* tcr_sw;
@@ -402,6 +412,8 @@ Persist carve_persist(const Plan& P, const pt_params* p, void* base, size_t* byt
     q.tck_R = c.take<TcKey>(P.tk_R.size());
     q.tck_sw = c.take<TcKey>(P.tk_sw.size());
     q.tc_max = c.take<unsigned long long>(4);
+    q.oz_a = c.take<__half>((size_t)oz_slices() * rowsA * P.ldtc);
+    q.oz_e = c.take<int>(rowsA);
   }
   q.m_ext = c.take<double>((size_t)P.Nz * P.nt);
   q.nn_theta = c.take<float>(kNnParams);
@@ -446,6 +458,8 @@ struct SolveBufs {
   cd* tbuf;         // PLR projections
   __half *tc_bhi, *tc_blo;  // staged tensor-core operands
   float *tc_scale, *tc_inv;
+  __half* oz_x;     // staged input slices of the split restart product
+  int* oz_f;        // per-source exponents of those inputs
   double* vres;     // volume residual partials
   double* nn_rms;   // learned correction: per-source RMS of the input
   float *nn_X, *nn_A, *nn_Y;  // features, two W x P activation buffers, outputs
@@ -491,6 +505,8 @@ SolveBufs carve_solve(const Plan& P, int S, int m, bool host_staging, void* base
     b.tc_blo = c.take<__half>(el);
     b.tc_scale = c.take<float>(S);
     b.tc_inv = c.take<float>(S);
+    b.oz_x = c.take<__half>((size_t)oz_slices() * P.tk_mv.size() * 2 * S * P.ldtc);
+    b.oz_f = c.take<int>(S);
   }
   b.vres = c.take<double>((size_t)S + (size_t)S * 2 * 512);
   if (P.learned) {
@@ -709,6 +725,10 @@ struct pt_ctx {
   // tensor-core form
   int eA = 0;
   CUtensorMap mapAhi, mapAlo, mapBhi, mapBlo;
+  CUtensorMap mapOzA, mapOzX;  // slices of the blocks and of the staged inputs (split restart product)
+  __half* oz_x = nullptr;
+  int* oz_f = nullptr;
+  int opt_restart = 1;      // PT_OPT_RESTART (PT_MIXED_TC)
   int tc_bn = 0, tc_S = 0;
   __half *tc_bhi = nullptr, *tc_blo = nullptr;
   float *tc_scale = nullptr, *tc_inv = nullptr;
@@ -892,6 +912,10 @@ static pt_status prepare_tc(pt_ctx* c) {
   if (!tc_make_map(&c->mapAhi, c->d.tc_ahi, rowsA, P.ldtc, P.ldtc, 128) ||
       !tc_make_map(&c->mapAlo, c->d.tc_alo, rowsA, P.ldtc, P.ldtc, 128))
     return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the block rows");
+  // slices of the blocks for the split restart product (exact tensor-core accumulation)
+  PT_CUDA(launch_oz_blocks(c->d.blocks, rowsA, P.nt, P.ldtc, c->d.oz_a, c->d.oz_e, s));
+  if (!tc_make_map(&c->mapOzA, c->d.oz_a, (size_t)oz_slices() * rowsA, P.ldtc, P.ldtc, 128))
+    return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the block slices");
   PT_CUDA(cudaStreamSynchronize(s));
   return PT_OK;
 }
@@ -1005,6 +1029,11 @@ static pt_status bind_call(pt_ctx* c, const SolveBufs& B, int S) {
   if (!tc_make_map(&c->mapBhi, B.tc_bhi, rows, c->P.ldtc, c->P.ldtc, c->tc_bn) ||
       !tc_make_map(&c->mapBlo, B.tc_blo, rows, c->P.ldtc, c->P.ldtc, c->tc_bn))
     return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the staged operands");
+  c->oz_x = B.oz_x;
+  c->oz_f = B.oz_f;
+  if (!tc_make_map(&c->mapOzX, B.oz_x, (size_t)oz_slices() * c->P.tk_mv.size() * two_s, c->P.ldtc, c->P.ldtc,
+                   oz_bn()))
+    return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the staged input slices");
   c->tc_S = S;
   return PT_OK;
 }
@@ -1128,6 +1157,19 @@ cudaError_t do_matvec(pt_ctx* c, int S, const cd* x, cd* y, bool exact = true) {
 // about twice its time), which in PT_MIXED_TC also corrects the ~1e-5 tensor-core matvec of
 // the inner cycles
 cudaError_t do_restart_matvec(pt_ctx* c, int S, const cd* x, cd* y) {
+  if (tcmode(c) && c->opt_restart == 1) {
+    // split products on the tensor cores (exact FP32 accumulation per 512-long segment, ~1e-10)
+    const Plan& P = c->P;
+    const int nk = (int)P.tk_mv.size();
+    c->launches += 3;
+    cudaError_t e = launch_oz_source_exp(x, P.N, S, c->oz_f, c->stream);
+    if (e == cudaSuccess)
+      e = launch_oz_stage(c->d.tck_mv, nk, x, P.nt, P.T4, S, P.ldtc, c->oz_f, (size_t)nk * 2 * S, c->oz_x, c->stream);
+    if (e == cudaSuccess)
+      e = launch_oz_apply(c->mapOzA, c->mapOzX, c->d.tcr_mv, P.T4, P.nt, P.T4, S, (int)((size_t)P.L * 16 * P.nt),
+                          nk * 2 * S, c->d.oz_e, c->oz_f, x, nullptr, y, 1.0, 0.0, c->d.status, c->stream);
+    return e;
+  }
   if (mixed(c) && !c->P.plr) return apply(c, kModeDF, op_matvec(c), S, x, nullptr, y, kApplyRowsWide, 1.0, 0.0, false);
   return do_matvec(c, S, x, y);
 }
@@ -1309,6 +1351,12 @@ extern "C" pt_status pt_set_option(pt_ctx* ctx, int32_t option, int32_t value) {
     if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_PRECOND_FP16 must be 0 or 1");
     if (value == 1 && !ctx->d.blocks_h16) return fail(PT_ERR_ARG, "FP16 preconditioner blocks need PT_MIXED_FP32, plr = 0");
     ctx->opt_precond16 = value;
+    return PT_OK;
+  }
+  if (option == PT_OPT_RESTART) {
+    if (value != 0 && value != 1) return fail(PT_ERR_ARG, "PT_OPT_RESTART must be 0 or 1");
+    if (!tcmode(ctx)) return fail(PT_ERR_ARG, "PT_OPT_RESTART needs PT_MIXED_TC");
+    ctx->opt_restart = value;
     return PT_OK;
   }
   if (option == PT_OPT_RELAX) {

@@ -306,6 +306,322 @@ __global__ void max_abs_kernel(const cd* __restrict__ v, size_t n, unsigned long
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));  // m >= 0: bit order = value order
 }
 
+// ---- Exact split products for the explicit residual of a restart (tensor cores) -----------
+// The error-free splitting of Ozaki, Ogita, Oishi and Rump (2012) for matrix products: each
+// operand row is scaled by a power of two into (-1, 1) and cut into kOzP slices of kOzW bits,
+//     v = 2^e sum_i a_i 2^{-7 i},   a_1 = rint(2^7 R_0), a_{i+1} = rint(2^7 R_i),
+//     R_0 = v 2^-e, R_i = 2^7 R_{i-1} - a_i,
+// with integer slices |a_1| <= 128, |a_i| <= 64 (i > 1), held exactly in FP16.  A product of two
+// slices is an integer below 2^14, and a sum of 512 of them at one level i + j stays below 2^24,
+// so the tensor cores' FP32 accumulation of one 512-long K segment is exact; the segments are
+// added into double-float accumulators with power-of-two weights 2^{-7 (i + j)}.  Slice pairs
+// with i + j > kOzLevels + 1 (1-based) are dropped: the product keeps about 35 bits, relative to
+// the largest entry of the block row times the largest entry of the source's vector (~1e-10
+// on the blocks of the jump system, against ~1e-14 for double-float and 1e-5 for the
+// three-pass FP16 matvec).
+constexpr int kOzW = 7;
+constexpr int kOzP = 5;          // slices per operand
+constexpr int kOzLevels = 5;     // 0-based levels i + j = 0 .. 4: 15 slice pairs
+constexpr int kOzBN = 48;        // output columns (real parts / imaginary parts of sources) per CTA
+constexpr int kOzStages = 2;
+constexpr int kOzSegBlocks = 8;  // K blocks (of 64) per exact segment
+constexpr int kOzThreads = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: accumulators and epilogue
+
+// Offline: block rows [Br Bi] (FP64) to kOzP FP16 slice arrays (slice-major, ld halves per row,
+// padding zero) and the row exponents e with max |row| < 2^e; one warp per block row.
+__global__ void oz_blocks_kernel(const cd* __restrict__ blocks, size_t nrows, int nt, int ld,
+                                 __half* __restrict__ out, int* __restrict__ ex) {
+  const int lane = threadIdx.x & 31;
+  const size_t w0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+  const size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t q = w0; q < nrows; q += nw) {
+    const cd* row = blocks + q * nt;
+    double m = 0.0;
+    for (int k = lane; k < nt; k += 32) m = fmax(m, fmax(fabs(row[k].x), fabs(row[k].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);  // m in [2^(e-1), 2^e)
+    for (int k = lane; k < ld; k += 32) {
+      double v = 0.0;
+      if (k < nt) v = row[k].x;
+      else if (k < 2 * nt) v = row[k - nt].y;
+      double R = ldexp(v, -e);
+#pragma unroll
+      for (int i = 0; i < kOzP; ++i) {
+        R *= 128.0;
+        const double a = rint(R);
+        R -= a;
+        out[(size_t)i * nrows * ld + q * ld + k] = __double2half(a);
+      }
+    }
+    if (lane == 0) ex[q] = e;
+  }
+}
+
+// Per-source exponent f with max |x_s| < 2^(f - 1): staged inputs sum two traces at most.
+__global__ void oz_source_exp_kernel(const cd* __restrict__ x, size_t per_src, int* __restrict__ fexp) {
+  const int s = blockIdx.x;
+  double m = 0.0;
+  for (size_t k = threadIdx.x; k < per_src; k += blockDim.x) {
+    const cd v = x[(size_t)s * per_src + k];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
+    int e = 0;
+    if (mm > 0.0) frexp(mm, &e);
+    fexp[s] = mm > 0.0 ? e + 1 : 0;
+  }
+}
+
+// Staged input slices of key k for source s (rows k 2S + s: [Re X | -Im X], k 2S + S + s:
+// [Im X | Re X]) in kOzP slice-major arrays of slice_rows rows, X = sign (x[in1] + x[in2]).
+__global__ void oz_stage_kernel(const TcKey* __restrict__ keys, int nkeys, const cd* __restrict__ x, int nt, int T4,
+                                int S, int ld, const int* __restrict__ fexp, size_t slice_rows,
+                                __half* __restrict__ out) {
+  const int half_ld = ld / 2;
+  const size_t total = (size_t)nkeys * S * half_ld;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q / ((size_t)S * half_ld));
+    const size_t rem = q - (size_t)k * S * half_ld;
+    const int s = (int)(rem / half_ld), j = (int)(rem - (size_t)s * half_ld);
+    const size_t rr = ((size_t)k * 2 * S + s) * ld, ri = ((size_t)k * 2 * S + S + s) * ld;
+    if (j >= nt) {  // padding columns 2 nt .. ld of both rows, every slice
+      const int c = 2 * nt + 2 * (j - nt);
+      for (int i = 0; i < kOzP; ++i)
+        for (int d = 0; d < 2; ++d)
+          if (c + d < ld) {
+            out[(size_t)i * slice_rows * ld + rr + c + d] = __float2half(0.f);
+            out[(size_t)i * slice_rows * ld + ri + c + d] = __float2half(0.f);
+          }
+      continue;
+    }
+    const TcKey key = keys[k];
+    const cd* xs = x + (size_t)s * T4 * nt;
+    cd v = xs[(size_t)key.in1 * nt + j];
+    if (key.in2 >= 0) v = cadd(v, xs[(size_t)key.in2 * nt + j]);
+    const int f = fexp[s];
+    double Rr = ldexp(key.sign * v.x, -f), Ri = ldexp(key.sign * v.y, -f);
+#pragma unroll
+    for (int i = 0; i < kOzP; ++i) {
+      Rr *= 128.0;
+      Ri *= 128.0;
+      const double ar = rint(Rr), ai = rint(Ri);
+      Rr -= ar;
+      Ri -= ai;
+      __half* o = out + (size_t)i * slice_rows * ld;
+      const __half hr = __double2half(ar), hi = __double2half(ai), mhi = __double2half(-ai);
+      o[rr + j] = hr;
+      o[rr + nt + j] = mhi;
+      o[ri + j] = hi;
+      o[ri + nt + j] = hr;
+    }
+  }
+}
+
+// (hi, lo) += v for an FP32 v (Knuth's two-sum; the error term collected in lo)
+__device__ __forceinline__ void oz_acc(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+__device__ __forceinline__ float oz_pow2(int E) { return E < -126 ? 0.f : ldexpf(1.0f, E); }
+
+// One CTA per 128 x kOzBN output tile of one output trace (grid z) of the operator table: y =
+// alpha (sum of the terms' block products + identity terms) + beta aux, the block products by
+// the split products above.  Two shared-memory stages, each holding the kOzP slices of a
+// 128 x 64 block-row tile and of a kOzBN x 64 input tile (128-byte swizzle); five FP32
+// accumulators (levels) of kOzBN columns in tensor memory, reset every segment.
+__global__ void __launch_bounds__(kOzThreads, 1) oz_apply_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, const TcRow* __restrict__ rows,
+    int nt, int T4, int S, int a_slice_rows, int x_slice_rows, const int* __restrict__ aexp,
+    const int* __restrict__ fexp, const cd* x, const cd* __restrict__ aux, cd* y, double alpha, double beta,
+    int* status) {
+  constexpr int A_BYTES = kTcBM * kTcBK * 2, X_BYTES = kOzBN * kTcBK * 2;
+  constexpr int STAGE = kOzP * (A_BYTES + X_BYTES);
+  constexpr uint32_t kIdesc =
+      (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kOzBN >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
+  extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kOzStages], empty[kOzStages], seg_full, seg_free, done;
+  __shared__ uint32_t tmem_base;
+  __shared__ TcRow row;
+  __shared__ int abort_flag, issued, consumed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * kOzBN;
+  if (threadIdx.x == 0) {
+    row = rows[blockIdx.z];
+    for (int s = 0; s < kOzStages; ++s) {
+      tc_mb_init(&full[s], 1);
+      tc_mb_init(&empty[s], 1);
+    }
+    tc_mb_init(&seg_full, 1);
+    tc_mb_init(&seg_free, 4);
+    tc_mb_init(&done, 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int nkb = (2 * nt + kTcBK - 1) / kTcBK;
+  const int segs_per_term = (nkb + kOzSegBlocks - 1) / kOzSegBlocks;
+  const int total = row.nterms * nkb;
+  const int nseg = row.nterms * segs_per_term;
+
+  if (warp == 0 && lane == 0) {  // ---- TMA producer
+    int it = 0;
+    for (; it < total; ++it) {
+      const int s = it % kOzStages, u = it / kOzStages;
+      if (it >= kOzStages && !tc_mb_wait(&empty[s], (u & 1) ^ 1, status)) { atomicExch(&abort_flag, 1); break; }
+      if (*(volatile int*)&abort_flag) break;
+      const int t = it / nkb, kb = it - t * nkb;
+      unsigned char* st = smem + s * STAGE;
+      tc_mb_expect(&full[s], STAGE);
+      for (int i = 0; i < kOzP; ++i)
+        tc_tma_2d(st + i * A_BYTES, &tmA, kb * kTcBK, i * a_slice_rows + row.t[t].a_row0 + m0, &full[s]);
+      for (int j = 0; j < kOzP; ++j)
+        tc_tma_2d(st + kOzP * A_BYTES + j * X_BYTES, &tmX, kb * kTcBK, j * x_slice_rows + row.t[t].key * 2 * S + n0,
+                  &full[s]);
+    }
+    issued = it;
+  } else if (warp == 1 && lane == 0) {  // ---- MMA issuer
+    int it = 0, seg = 0;
+    for (; it < total; ++it) {
+      const int s = it % kOzStages, u = it / kOzStages;
+      const int t = it / nkb, kb = it - t * nkb;
+      const bool first = kb % kOzSegBlocks == 0;
+      const bool last = kb % kOzSegBlocks == kOzSegBlocks - 1 || kb == nkb - 1;
+      // the accumulators of the previous segment must have been read before they are reset
+      if (first && seg > 0 && !tc_mb_wait(&seg_free, (seg - 1) & 1, status)) { atomicExch(&abort_flag, 1); break; }
+      if (!tc_mb_wait(&full[s], u & 1, status)) { atomicExch(&abort_flag, 1); break; }
+      if (*(volatile int*)&abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = tc_saddr(smem + s * STAGE), x0 = a0 + kOzP * A_BYTES;
+      uint32_t fresh = first ? 0x1Fu : 0u;  // levels not yet written in this segment
+#pragma unroll 1
+      for (int i = 0; i < kOzP; ++i) {
+#pragma unroll 1
+        for (int j = 0; i + j < kOzLevels; ++j) {
+          const int l = i + j;
+          const uint32_t d = tmem + (uint32_t)(l * 64);
+#pragma unroll
+          for (int kk = 0; kk < kTcBK / 16; ++kk) {
+            const uint64_t ad = tc_sdesc(a0 + i * A_BYTES + kk * 32), bd = tc_sdesc(x0 + j * X_BYTES + kk * 32);
+            const uint32_t acc = (fresh >> l) & 1u ? 0u : 1u;
+            fresh &= ~(1u << l);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc_saddr(&empty[s]))
+                   : "memory");
+      if (last) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc_saddr(&seg_full))
+                     : "memory");
+        ++seg;
+      }
+    }
+    consumed = it;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_saddr(&done))
+                 : "memory");
+  } else if (warp >= 2) {  // ---- accumulators and epilogue: warp w reads TMEM lanes 32 (w % 4) ..
+    const int quarter = warp & 3;
+    const int r = m0 + quarter * 32 + lane;
+    int et[4] = {0, 0, 0, 0}, eref = -100000;
+    for (int t = 0; t < row.nterms; ++t) {
+      et[t] = r < nt ? aexp[row.t[t].a_row0 + r] : 0;
+      eref = max(eref, et[t]);
+    }
+    float hi[kOzBN], lo[kOzBN];
+#pragma unroll
+    for (int c = 0; c < kOzBN; ++c) hi[c] = lo[c] = 0.f;
+    bool ok = true;
+    for (int seg = 0; seg < nseg && ok; ++seg) {
+      ok = tc_mb_wait(&seg_full, seg & 1, status) && !*(volatile int*)&abort_flag;
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) { atomicExch(&abort_flag, 1); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int t = seg / segs_per_term;
+#pragma unroll 1
+      for (int l = 0; l < kOzLevels; ++l) {
+        const float w = oz_pow2(et[t] - eref - kOzW * (l + 2));
+#pragma unroll
+        for (int cc = 0; cc < kOzBN / 16; ++cc) {
+          uint32_t v[16];
+          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(l * 64 + cc * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 16; ++q) oz_acc(hi[cc * 16 + q], lo[cc * 16 + q], __fmul_rn(__uint_as_float(v[q]), w));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_saddr(&seg_free)) : "memory");
+    }
+    // ---- epilogue: y = alpha (2^(eref + f_s) (hi + lo) + identity terms) + beta aux
+    if (ok && r < nt) {
+      const size_t vs = (size_t)T4 * nt;
+#pragma unroll
+      for (int c = 0; c < kOzBN; ++c) {  // unrolled: hi / lo stay in registers
+        const int col = n0 + c;
+        if (col >= 2 * S) continue;
+        const int s = col < S ? col : col - S;
+        const bool im = col >= S;
+        double val = ldexp((double)hi[c] + (double)lo[c], eref + fexp[s]);
+        const cd* xs = x + (size_t)s * vs;
+        const cd* as = aux ? aux + (size_t)s * vs : nullptr;
+        for (int e = 0; e < row.nid; ++e) {
+          const cd* src = row.id_src[e] == 0 ? xs : as;
+          const cd q = src[(size_t)row.id_trace[e] * nt + r];
+          val += row.id_sign[e] * (im ? q.y : q.x);
+        }
+        val *= alpha;
+        if (beta != 0.0) {
+          const cd q = as[(size_t)row.out * nt + r];
+          val += beta * (im ? q.y : q.x);
+        }
+        reinterpret_cast<double*>(y + (size_t)s * vs + (size_t)row.out * nt + r)[im ? 1 : 0] = val;
+      }
+    }
+  }
+  __syncthreads();
+  // teardown: every MMA has completed (done), every issued copy has landed, then TMEM is freed
+  if (threadIdx.x == 32) tc_mb_wait(&done, 0, status);
+  if (threadIdx.x == 0)
+    for (int it = consumed; it < issued; ++it) tc_mb_wait(&full[it % kOzStages], (it / kOzStages) & 1, status);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 // ---- host side -----------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -379,6 +695,34 @@ cudaError_t launch_tc_apply(int bn, const CUtensorMap& ahi, const CUtensorMap& a
                                                   beta, status);
   }
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+size_t oz_smem_bytes() { return (size_t)kOzStages * kOzP * (kTcBM * kTcBK * 2 + kOzBN * kTcBK * 2) + 1024; }
+int oz_slices() { return kOzP; }
+int oz_bn() { return kOzBN; }
+
+cudaError_t launch_oz_blocks(const cd* blocks, size_t nrows, int nt, int ld, __half* out, int* ex, cudaStream_t s) {
+  oz_blocks_kernel<<<1216, 256, 0, s>>>(blocks, nrows, nt, ld, out, ex);
+  return cudaGetLastError();
+}
+cudaError_t launch_oz_source_exp(const cd* x, size_t per_src, int nsrc, int* fexp, cudaStream_t s) {
+  oz_source_exp_kernel<<<nsrc, 256, 0, s>>>(x, per_src, fexp);
+  return cudaGetLastError();
+}
+cudaError_t launch_oz_stage(const TcKey* keys, int nkeys, const cd* x, int nt, int T4, int S, int ld, const int* fexp,
+                            size_t slice_rows, __half* out, cudaStream_t s) {
+  oz_stage_kernel<<<2432, 256, 0, s>>>(keys, nkeys, x, nt, T4, S, ld, fexp, slice_rows, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_oz_apply(const CUtensorMap& tmA, const CUtensorMap& tmX, const TcRow* rows, int nrows, int nt, int T4,
+                            int S, int a_slice_rows, int x_slice_rows, const int* aexp, const int* fexp, const cd* x,
+                            const cd* aux, cd* y, double alpha, double beta, int* status, cudaStream_t s) {
+  dim3 grid((nt + kTcBM - 1) / kTcBM, (2 * S + kOzBN - 1) / kOzBN, nrows);
+  cudaError_t e = smem_limit_max(reinterpret_cast<const void*>(oz_apply_kernel));
+  if (e != cudaSuccess) return e;
+  oz_apply_kernel<<<grid, kOzThreads, oz_smem_bytes(), s>>>(tmA, tmX, rows, nt, T4, S, a_slice_rows, x_slice_rows, aexp,
+                                                            fexp, x, aux, y, alpha, beta, status);
   return cudaGetLastError();
 }
 
