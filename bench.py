@@ -474,6 +474,25 @@ def headline_section(args, dev, pg, pk, oracle, world):
     t_mv = time_apply(tc, "matvec", x, stream)  # three FP16 hi/lo passes, the GMRES matvec
     t_rs = time_apply(tc, "restart", x, stream)  # double-float P M, the explicit residual of a restart
     t_dinv = time_apply(tc, "Dinv", x, stream)   # one FP16 pass, 31 sweep steps
+    t_R = time_apply(tc, "R", x, stream)         # one FP16 pass
+    # the reconstruction: solves with and without the volume output
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+    t_with, t_without = [], []
+    for _ in range(2):
+        ev[0][0].record(stream)
+        tc.solve(f, tol=wl.tol, u=u, want_traces=False)
+        ev[0][1].record(stream)
+        ev[1][0].record(stream)
+        tc.solve(f, tol=wl.tol, want_u=False, want_traces=False)
+        ev[1][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_with.append(ev[0][0].elapsed_time(ev[0][1]))
+        t_without.append(ev[1][0].elapsed_time(ev[1][1]))
+    out["time_split_ms"] = {"matvec_3pass": t_mv * 1e3, "Dinv": t_dinv * 1e3, "R": t_R * 1e3,
+                            "restart_product": t_rs * 1e3,
+                            "reconstruction": statistics.median(t_with) - statistics.median(t_without),
+                            "note": "one call each over all sources; a GMRES iteration is one matvec and n_it = 2 "
+                                    "sweeps D^-1 with one R between them"}
     cplx_mv = 8.0 * nblocks_mv * wl.nt * wl.nt * S
     peak_tc = pk.get("bf16_tflops")
     roof_tc = {"kernel": "tc_apply_kernel (tcgen05 FP16 x FP16 -> FP32, GMRES matvec, three hi/lo passes)",
@@ -839,7 +858,8 @@ def main():
         "volume_rel_err_vs_oracle": head["volume_rel_err_vs_oracle"],
         "volume_residual_max": head["volume_residual_max"], "offline_s": head["offline_s"],
         "roofline": head["roofline_tc_matvec"], "roofline_restart": head["roofline_restart"],
-        "roofline_tc_dinv": head["roofline_tc_dinv"], "peaks_source": pk_kind, "clocks": head["clocks"],
+        "roofline_tc_dinv": head["roofline_tc_dinv"], "time_split_ms": head["time_split_ms"],
+        "peaks_source": pk_kind, "clocks": head["clocks"],
         "e2e": head["e2e"], "gpu_launches": int(head["launches_per_step"] * args.steps), "cpu_baseline": cpu,
     }
     if "plain_fp64" in head:

@@ -726,6 +726,8 @@ struct pt_ctx {
   int eA = 0;
   CUtensorMap mapAhi, mapAlo, mapBhi, mapBlo;
   CUtensorMap mapOzA, mapOzX;  // slices of the blocks and of the staged inputs (split restart product)
+  CUtensorMap mapBsw;          // staged inputs with the narrower column tile of the sweep steps
+  int tc_bn_sw = 0;
   __half* oz_x = nullptr;
   int* oz_f = nullptr;
   int opt_restart = 1;      // PT_OPT_RESTART (PT_MIXED_TC)
@@ -1025,10 +1027,14 @@ static pt_status bind_call(pt_ctx* c, const SolveBufs& B, int S) {
   c->tc_inv = B.tc_inv;
   const int two_s = 2 * S;
   c->tc_bn = two_s <= 64 ? 64 : (two_s <= 128 ? 128 : 256);
+  // a sweep step has only four output traces: narrower column tiles give it more CTAs
+  c->tc_bn_sw = std::min(c->tc_bn, 128);
   const size_t rows = (size_t)c->P.tc_keys_max * two_s;
   if (!tc_make_map(&c->mapBhi, B.tc_bhi, rows, c->P.ldtc, c->P.ldtc, c->tc_bn) ||
       !tc_make_map(&c->mapBlo, B.tc_blo, rows, c->P.ldtc, c->P.ldtc, c->tc_bn))
     return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the staged operands");
+  if (!tc_make_map(&c->mapBsw, B.tc_bhi, rows, c->P.ldtc, c->P.ldtc, c->tc_bn_sw))
+    return fail(PT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the staged operands of the sweeps");
   c->oz_x = B.oz_x;
   c->oz_f = B.oz_f;
   if (!tc_make_map(&c->mapOzX, B.oz_x, (size_t)oz_slices() * c->P.tk_mv.size() * two_s, c->P.ldtc, c->P.ldtc,
@@ -1055,6 +1061,7 @@ struct OpRef {
   const TcRow* tcr;      // tensor-core rows and staged-input keys (PT_MIXED_TC)
   const TcKey* tck;
   int nkeys;
+  bool sweep = false;    // one sweep step (four output traces)
 };
 
 // Dense apply in the given arithmetic mode, or the PLR apply when the context
@@ -1069,6 +1076,9 @@ cudaError_t apply(pt_ctx* c, int mode, const OpRef& op, int S, const cd* x, cons
     cudaError_t e = launch_tc_stage(op.tck, op.nkeys, x, P.nt, P.T4, S, P.ldtc, c->tc_scale, c->tc_bhi,
                                     npass == 3 ? c->tc_blo : nullptr, c->stream);
     if (e != cudaSuccess) return e;
+    if (op.sweep && npass == 1)
+      return launch_tc_apply(c->tc_bn_sw, c->mapAhi, c->mapAlo, c->mapBsw, c->mapBlo, op.tcr, op.nrows, P.nt, P.T4,
+                             S, npass, c->tc_inv, x, aux, y, alpha, beta, c->d.status, c->stream);
     return launch_tc_apply(c->tc_bn, c->mapAhi, c->mapAlo, c->mapBhi, c->mapBlo, op.tcr, op.nrows, P.nt, P.T4, S,
                            npass, c->tc_inv, x, aux, y, alpha, beta, c->d.status, c->stream);
   }
@@ -1117,7 +1127,7 @@ OpRef op_R(pt_ctx* c) {
                (int)c->P.tk_R.size()};
 }
 OpRef op_sweep(pt_ctx* c, int step) {
-  OpRef o{c->d.tab_sweep + 4 * step, 4, nullptr, 0, nullptr, nullptr, nullptr, 0};
+  OpRef o{c->d.tab_sweep + 4 * step, 4, nullptr, 0, nullptr, nullptr, nullptr, 0, true};
   if (c->P.plr) {
     o.tasks = c->d.task_sw + c->sw_off[step];
     o.ntasks = c->sw_cnt[step];

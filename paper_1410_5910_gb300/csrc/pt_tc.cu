@@ -171,26 +171,26 @@ __global__ void __launch_bounds__(128) tc_apply_kernel(
         for (int j = 0; j < 32; ++j) v[j] = 0u;  // no block term: only the identity terms remain
       }
       if (r < nt) {
+        // FP32 arithmetic (the products carry ~1e-5 at best): GB300's FP64 pipe takes 16 cycles per
+        // warp instruction, and an FP64 epilogue over 128 x BN outputs outlasted the MMAs of a sweep
+        // step; FP64 only for the loads, one conversion each, and the store
+        const float fa = (float)alpha, fb = (float)beta;
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + cc * 32 + j;
           if (col >= 2 * S) break;
           const int s = col < S ? col : col - S;
-          const bool im = col >= S;
-          double val = (double)__uint_as_float(v[j]) * (double)inv_scale[s];
+          const int im = col >= S ? 1 : 0;
+          float val = __uint_as_float(v[j]) * inv_scale[s];
           const cd* xs = x + (size_t)s * vs;
           const cd* as = aux ? aux + (size_t)s * vs : nullptr;
           for (int e = 0; e < row.nid; ++e) {
             const cd* src = row.id_src[e] == 0 ? xs : as;
-            const cd q = src[(size_t)row.id_trace[e] * nt + r];
-            val += row.id_sign[e] * (im ? q.y : q.x);
+            const double q = reinterpret_cast<const double*>(src + (size_t)row.id_trace[e] * nt + r)[im];
+            val += (row.id_sign[e] > 0.0 ? 1.0f : -1.0f) * __double2float_rn(q);
           }
-          val *= alpha;
-          if (beta != 0.0) {
-            const cd q = as[(size_t)row.out * nt + r];
-            val += beta * (im ? q.y : q.x);
-          }
-          double* dst = reinterpret_cast<double*>(y + (size_t)s * vs + (size_t)row.out * nt + r);
-          dst[im ? 1 : 0] = val;
+          val *= fa;
+          if (beta != 0.0) val += fb * __double2float_rn(reinterpret_cast<const double*>(as + (size_t)row.out * nt + r)[im]);
+          reinterpret_cast<double*>(y + (size_t)s * vs + (size_t)row.out * nt + r)[im] = (double)val;
         }
       }
     }
@@ -255,23 +255,28 @@ __global__ void tc_stage_kernel(const TcKey* __restrict__ keys, int nkeys, const
     }
     const TcKey key = keys[k];
     const cd* xs = x + (size_t)s * T4 * nt;
-    cd v = xs[(size_t)key.in1 * nt + j];
-    if (key.in2 >= 0) v = cadd(v, xs[(size_t)key.in2 * nt + j]);
-    const double sc = key.sign * (double)scale[s];
-    const double re = v.x * sc, imv = v.y * sc;
-    const __half rh = __double2half(re), ih = __double2half(imv);
-    const __half mih = __double2half(-imv);
+    // FP32 arithmetic: the hi / lo split keeps 22 bits (FP32 has 24); FP64 only for the loads
+    const cd a = xs[(size_t)key.in1 * nt + j];
+    float vr = __double2float_rn(a.x), vi = __double2float_rn(a.y);
+    if (key.in2 >= 0) {
+      const cd b = xs[(size_t)key.in2 * nt + j];
+      vr += __double2float_rn(b.x);
+      vi += __double2float_rn(b.y);
+    }
+    const float sc = (key.sign > 0.0 ? 1.0f : -1.0f) * scale[s];
+    const float re = vr * sc, imv = vi * sc;
+    const __half rh = __float2half_rn(re), ih = __float2half_rn(imv);
+    const __half mih = __hneg(ih);
     const size_t rr = ((size_t)k * 2 * S + s) * ld, ri = ((size_t)k * 2 * S + S + s) * ld;
     hi[rr + j] = rh;
     hi[rr + nt + j] = mih;
     hi[ri + j] = ih;
     hi[ri + nt + j] = rh;
     if (lo) {
-      const __half rl = __double2half(re - (double)__half2float(rh));
-      const __half il = __double2half(imv - (double)__half2float(ih));
-      const __half mil = __double2half(-imv - (double)__half2float(mih));
+      const __half rl = __float2half_rn(re - __half2float(rh));
+      const __half il = __float2half_rn(imv - __half2float(ih));
       lo[rr + j] = rl;
-      lo[rr + nt + j] = mil;
+      lo[rr + nt + j] = __hneg(il);
       lo[ri + j] = il;
       lo[ri + nt + j] = rl;
     }
