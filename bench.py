@@ -719,6 +719,103 @@ def uneven_section(args, dev, pg):
 
 
 
+# ---- experiments (not part of the default run; one JSON line each) -----------------------------
+def _grf_case(nx: int, nz: int, L: int, ppw: float, seed: int = 7) -> W.Workload:
+    return W.Workload(f"grf-{nx}x{nz}-L{L}-ppw{ppw:.1f}", nx, nz, 20, L, ppw, "grf", seed, ((nx // 2 + 1, 10),),
+                      1e-7)
+
+
+def experiment_hf_sweep(args, dev):
+    """The paper's two frequency regimes (Section 7 tables) on the GRF family: omega ~ n (fixed points per
+    wavelength) and omega ~ sqrt(n) (points per wavelength growing like sqrt(n)), n_x x n_z with n_z ~ 4 n_x,
+    layered along z.  Per case: GMRES iterations and time per solve and per iteration (mixed form, one source
+    near the top, tol 1e-7), FP64 iterations, and the partitioned low-rank storage of the blocks
+    (eps = 1e-9 / L, r_max = ceil(sqrt(n_t)), Section 5.1) for the compression-scaling fit."""
+    import math
+
+    import torch
+
+    from paper_1410_5910_gb300 import PT_FP64, PT_MIXED_FP32
+
+    sizes = [(127, 511, (8, 16)), (255, 1023, (16, 32)), (511, 2047, (32,))]
+    out = []
+    stream = torch.cuda.current_stream(dev)
+    for regime in ("omega~n", "omega~sqrt(n)"):
+        for nx, nz, Ls in sizes:
+            ppw = 10.0 if regime == "omega~n" else 10.0 * math.sqrt(nx / 127.0)
+            for L in Ls:
+                wl = _grf_case(nx, nz, L, ppw)
+                c = wl.c_ext()
+                c_dev = torch.from_numpy(c).to(dev)
+                f = point_source_tensor(wl, wl.sources, device=dev)
+                rec = {"regime": regime, "nx": nx, "nz": nz, "N": nx * nz, "L": L, "ppw": ppw, "omega": wl.omega(c)}
+                sv, t_off = make_solver(wl, c, c_dev, PT_MIXED_FP32, 1, dev)
+                u = torch.empty_like(f)
+                ms, its, rel, _ = timed_solves(sv, f, u, 3, 3, wl.tol, dev, None, stream)
+                rec.update({"mixed_ms_per_solve": ms, "mixed_iterations": its[0], "mixed_ms_per_iteration": ms / its[0],
+                            "true_relres": rel[0], "offline_s": t_off})
+                del sv
+                rmax = int(math.ceil(math.sqrt(wl.nt)))
+                sp, _ = make_solver(wl, c, c_dev, PT_FP64, 1, dev, plr=True, plr_eps=1e-9 / L, plr_rmax=min(31, rmax))
+                ms64, its64, _, _ = timed_solves(sp, f, u, 2, 1, wl.tol, dev, None, stream)
+                stored, leaves = sp.plr_stats()
+                dense = (16 * (L - 2) + 8) * wl.nt * wl.nt
+                rec.update({"plr_fp64_iterations": its64[0], "plr_fp64_ms_per_solve": ms64, "plr_stored_entries": stored,
+                            "plr_leaves": leaves, "plr_compression": dense / stored, "plr_rmax": min(31, rmax)})
+                del sp, f, u, c_dev
+                torch.cuda.empty_cache()
+                out.append(rec)
+                print(json.dumps(rec), flush=True)
+    # compression scaling: stored entries of one interior layer's blocks against N, per regime
+    fits = {}
+    for regime in ("omega~n", "omega~sqrt(n)"):
+        pts = [(r["N"], r["plr_stored_entries"] / (16 * (r["L"] - 2) + 8)) for r in out
+               if r["regime"] == regime and r["L"] == max(x["L"] for x in out if x["nx"] == r["nx"])]
+        if len(pts) >= 2:
+            xs, ys = np.log([p[0] for p in pts]), np.log([p[1] for p in pts])
+            fits[regime] = float(np.polyfit(xs, ys, 1)[0])
+    print(json.dumps({"experiment": "hf-sweep", "cases": len(out), "compression_exponent_per_block_vs_N": fits,
+                      "note": "stored entries per block ~ N^p; dense blocks scale as N (n_t^2)"}), flush=True)
+
+
+def experiment_gs_vs_gmres(args, dev):
+    """Gauss-Seidel iteration as the solver (Algorithm 3) against flexible GMRES preconditioned by it
+    (Algorithm 4, n_it = 1, 2, 3), FP64 form, on the GRF 511 x 1023 (L = 16) and layered 255 x 511 (L = 8)
+    workloads, tol 1e-7: iterations and time per solve (Section 4.2 compares the two)."""
+    import torch
+
+    from paper_1410_5910_gb300 import PT_FP64
+
+    stream = torch.cuda.current_stream(dev)
+    for wl in (W.GRF_511x1023, W.LAYERED_255x511):
+        c = wl.c_ext()
+        c_dev = torch.from_numpy(c).to(dev)
+        f = point_source_tensor(wl, wl.sources[:1], device=dev)
+        rec = {"experiment": "gs-vs-gmres", "workload": wl.name}
+        for n_it in (1, 2, 3):
+            from paper_1410_5910_gb300 import PolarTrace, default_pml_strength
+
+            sv = PolarTrace(wl.nx, wl.nz, wl.npml, wl.L, wl.h, wl.omega(c), c_dev,
+                            pml_C=default_pml_strength(float(c.max())), precision=PT_FP64, gs_iters=n_it)
+            u = torch.empty_like(f)
+            ms, its, rel, _ = timed_solves(sv, f, u, 3, 2, 1e-7, dev, None, stream)
+            rec[f"gmres_n_it{n_it}"] = {"iterations": its[0], "ms_per_solve": ms, "true_relres": rel[0]}
+            if n_it == 2:
+                for _ in range(2):
+                    sv.solve_gs(f, tol=1e-7, max_it=500, allow_not_converged=True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, _, gits, grel = sv.solve_gs(f, tol=1e-7, max_it=500, allow_not_converged=True)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                rec["gauss_seidel"] = {"iterations": gits[0], "ms_per_solve": e0.elapsed_time(e1),
+                                       "true_relres": grel[0], "converged": gits[0] < 500,
+                                       "stop": "relative change of the iterate <= 1e-7 (Algorithm 3)"}
+            del sv
+            torch.cuda.empty_cache()
+        print(json.dumps(rec), flush=True)
+
+
 def top_config(args, world: int, omega: float) -> dict:
     """The ``config`` of the top-level line (both arms)."""
     wl = W.WORKLOADS[args.workload]
@@ -797,10 +894,19 @@ def main():
     ap.add_argument("--uneven-count", type=int, default=16)
     ap.add_argument("--uneven-nmax", type=int, default=511)
     ap.add_argument("--uneven-steps", type=int, default=2)
+    ap.add_argument("--experiment", default=None, choices=["hf-sweep", "gs-vs-gmres"],
+                    help="run one experiment instead of the benchmark (prints one JSON line per case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local, pg = dist_setup(args.gpus)
+    if args.experiment is not None:
+        import torch
+
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        {"hf-sweep": experiment_hf_sweep, "gs-vs-gmres": experiment_gs_vs_gmres}[args.experiment](args, dev)
+        return
 
     if args.impl == "reference":
         run_reference(args, rank)
